@@ -1,0 +1,303 @@
+#!/usr/bin/env python3
+"""Benchmark of the rigid-molecule MD hot path on GB300.
+
+Workload: the 2CLJQ rigid-molecule fluid (two LJ centres + a linear point
+quadrupole, elongation 0.5 sigma, Q*^2 = 2), N = 262,144 molecules, reduced
+density 0.55, T = 1, cut-off 3 sigma, LRC on, dt = 0.001 -- seeded synthetic
+input (no dataset).  One step = one md_step: leapfrog (translational +
+Fincham rotational) -> cell rebuild (counting sort) -> cell-pair force,
+torque, energy and virial kernel.
+
+Metric: site-pair interactions per second (interacting site pairs of the
+step's force evaluation / device time of the step), whole job; molecule
+updates per second reported beside it.  The working set (~90 MB) is below
+the 129 MB L2, so L2 is flushed (a 512 MB write) before every timed step,
+outside the timed events.
+
+--impl reference times the FP64 CPU oracle (the parity reference) on the
+host cores for the same workload and metric.
+"""
+import argparse
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import mdgen  # noqa: E402
+
+METRIC = "site-pair interactions/s and molecule updates/s at 1 GB300 (% FP32 roofline), vs oracle"
+UNIT = "site-pair interactions/s"
+KERNELS_PER_STEP = 8  # integrate, scan x3, scatter, in-cell sort, reorder+pack, force
+
+
+def flops_per_pair():
+    txt = open(os.path.join(ROOT, "include", "md_flops.h")).read()
+    return int(re.search(r"#define MD_FLOPS_PAIR_2CLJQ (\d+)", txt).group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        res = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.rows)}
+        if not self.rows:
+            return res
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        res["sm_mhz"] = float(np.median(sm)) if sm else None
+        res["sm_max_mhz"] = max(mx) if mx else None
+        res["reasons"] = sorted(reasons)
+        return res
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """FP64 CPU oracle on the host cores: one oracle step per bench step."""
+    if rank != 0:
+        return
+    import oracle
+    cfg = mdgen.config_2cljq()
+    s = oracle.setup_from_config(cfg)
+    cores = os.cpu_count()
+    st = {k: cfg[k] for k in ("r", "v", "q", "j")}
+    F, tau, _ = oracle.forces(cfg["model"], s, st["r"], st["q"], use_cells=True)
+    st["F"], st["tau"] = F, tau
+    for _ in range(args.warmup):
+        st = oracle.step(cfg["model"], s, st, cfg["dt"], 1, use_cells=True)
+    pairs = 0.0
+    t_tot = 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st = oracle.step(cfg["model"], s, st, cfg["dt"], 1, use_cells=True)
+        t_tot += time.perf_counter() - t0
+        pairs += st["obs"]["n_site_pairs"]
+    val = pairs / t_tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded 2CLJQ fluid)",
+            "config": {"workload": "2CLJQ rigid-molecule fluid N=262144 rho=0.55 T=1 rc=3 (one md step)",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full oracle leapfrog steps (linked cells, all cores)"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(seconds_budget=20.0):
+    """The oracle as it stands, timed on this host's cores on a bounded
+    sample of the bench workload (full-size force evaluations)."""
+    import oracle
+    cfg = mdgen.config_2cljq()
+    s = oracle.setup_from_config(cfg)
+    t0 = time.perf_counter()
+    n = 0
+    pairs = 0.0
+    while True:
+        _, _, o = oracle.forces(cfg["model"], s, cfg["r"], cfg["q"], use_cells=True)
+        n += 1
+        pairs += o["n_site_pairs"]
+        if time.perf_counter() - t0 > seconds_budget / 2 or n >= 8:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": pairs / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} full-size oracle force evaluations (linked cells, N=262144, all host cores)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--shell", default="half", choices=["half", "full"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    from paper_1408_4599_gb300 import md
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    cfg = mdgen.config_2cljq(seed_k=rank)
+    half = args.shell == "half"
+    sysm = md.System(cfg, deterministic=0 if half else 1, half_shell=1 if half else 0)
+    stream = torch.cuda.current_stream(dev)
+    t = {k: torch.from_numpy(cfg[k]).to(dev) for k in ("r", "v", "q", "j")}
+    sysm.set(t["r"], t["q"], t["v"], t["j"])
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        sysm.step(1, cfg["dt"])
+    sysm.observables()
+
+    md.md_profile(sysm.h, True)
+    md.md_kernel_times_get(sysm.h)  # reset
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    times, site_pairs, mol_pairs = [], 0, 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sysm.step(1, cfg["dt"])
+        e1.record(stream)
+        obs = sysm.observables()  # synchronises (outside the events)
+        times.append(e0.elapsed_time(e1))
+        site_pairs += obs["n_site_pairs"]
+        mol_pairs += obs["n_mol_pairs"]
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    kt = md.md_kernel_times_get(sysm.h)
+    md.md_profile(sysm.h, False)
+    t_ms = float(sum(times))
+    n_mol = cfg["r"].shape[0]
+
+    # whole job: units of all ranks / max time over ranks
+    tot = torch.tensor([site_pairs, mol_pairs, n_mol * args.steps], dtype=torch.float64, device=dev)
+    tmax = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(tot)
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+    t_s = float(tmax.item()) / 1e3
+    value = float(tot[0].item()) / t_s
+    mol_updates = float(tot[2].item()) / t_s
+
+    # roofline of the dominant kernel (force): counted FP32 FLOPs per launch
+    fk = kt["force"]
+    f_ms = fk["ms"] / max(fk["launches"], 1)
+    fpp = flops_per_pair()
+    flops_per_launch = fpp * (mol_pairs / args.steps)
+    achieved = flops_per_launch / (f_ms / 1e3) / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_force (2CLJQ, " + ("half" if half else "full") + " shell)",
+            "flops_per_pair": fpp, "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
+            f"{sm_max:.0f} MHz (FP32 FMA)",
+            "frac_at_sampled_clock": (achieved / (peak * clk["sm_mhz"] / sm_max)) if clk.get("sm_mhz") else None,
+            "force_ms_per_launch": f_ms}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 site math, f64 accumulation/state",
+            "data": "synthetic (seeded 2CLJQ fluid, random orientations)",
+            "config": {"workload": "2CLJQ rigid-molecule fluid N=262144 rho=0.55 T=1 rc=3 dt=0.001 (one md step)",
+                       "shell": args.shell, "l2": "flushed (512 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "molecule_updates_per_s": mol_updates,
+            "mol_pairs_per_step": mol_pairs / args.steps, "site_pairs_per_step": site_pairs / args.steps,
+            "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in kt.items() if v["launches"]},
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "roofline": roof, "clocks": clk}
+
+    if not args.no_e2e:
+        line["e2e"] = e2e_run(args, cfg, md, torch, dev)
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sysm.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def e2e_run(args, cfg, md, torch, dev):
+    """Same metric through the public API with host buffers: per step the
+    state is copied in from pinned host memory (md_set_molecules), advanced
+    one step (md_step, which recomputes the stale forces first), and the
+    state plus observables are read back (md_get_molecules,
+    md_energy_virial); all inside the timed region."""
+    n = cfg["r"].shape[0]
+    host = {k: torch.from_numpy(np.ascontiguousarray(cfg[k])).pin_memory() for k in ("r", "v", "q", "j")}
+    out = {k: torch.empty_like(host[k]).pin_memory() for k in host}
+    s = md.System(cfg, deterministic=0, half_shell=1 if args.shell == "half" else 0)
+    for _ in range(2):
+        s.set(host["r"], host["q"], host["v"], host["j"])
+        s.step(1, cfg["dt"])
+        s.molecules(r=out["r"], v=out["v"], q=out["q"], j=out["j"])
+    pairs = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.set(host["r"], host["q"], host["v"], host["j"])
+        s.step(1, cfg["dt"])
+        s.molecules(r=out["r"], v=out["v"], q=out["q"], j=out["j"])
+        pairs += s.observables()["n_site_pairs"]
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s.close()
+    return {"value": pairs / dt, "unit": UNIT, "h2d_bytes_per_step": n * 13 * 8,
+            "d2h_bytes_per_step": n * 13 * 8 + 160, "ms_per_step": 1e3 * dt / args.steps,
+            "note": "host->device state, md_step (incl. the stale-force evaluation), device->host state"}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * md.h -- C ABI of the GB300 (sm_103a) rigid multi-site molecular dynamics
+ * hot path described in "ls1 mardyn: The massively parallel molecular
+ * dynamics code for large systems" (Niethammer et al., arXiv 1408.4599).
+ *
+ * The library computes, on one GPU, the short-range forces, torques,
+ * potential energy and virial of rigid molecules made of Lennard-Jones
+ * centres, point charges, point dipoles and linear point quadrupoles
+ * (§2), over a linked-cell grid with a centre-of-mass cut-off and periodic
+ * boundaries (§3), with the reaction field for dipoles and the isotropic
+ * long-range correction for dispersion (§3), together with the cell rebuild
+ * and the leapfrog translational and rotational integrator (§3, Eqs. 2-5).
+ *
+ * Conventions shared by every entry point
+ *   - Reduced units; k_B = k_C = 1 (§2, units paragraph).
+ *   - Arrays are FP64, row-major: positions r, velocities v, angular
+ *     momenta j, forces F and torques tau are n x 3; quaternions q are
+ *     n x 4 as (w, x, y, z), unit, rotating body-frame vectors into the
+ *     space frame.  j is the space-frame angular momentum.
+ *   - Leapfrog state: v and j are half-step values v(t - dt/2), j(t - dt/2)
+ *     (Eqs. 2 and 4); r and q are at time t.
+ *   - Pointers flagged on_device are CUDA device pointers; otherwise host
+ *     pointers (pageable or pinned).  The library copies inputs; the caller
+ *     keeps ownership of every pointer it passes.  The library owns the
+ *     device state it allocates and frees it in md_destroy.
+ *   - cuda_stream is a cudaStream_t (NULL = the legacy default stream).
+ *     Calls marked "asynchronous" only enqueue work on that stream.
+ *   - Every function returns md_status; no exception crosses the ABI.
+ *     Arguments are validated before anything is launched.  Faults found
+ *     on the device (non-finite values, capacity overflow, a bounded wait
+ *     that ran out) are recorded in device flags and returned by the next
+ *     synchronising call (md_energy_virial, md_get_*, md_sync).
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef MD_H
+#define MD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct md_system md_system;
+typedef struct md_batch md_batch;
+
+typedef enum {
+    MD_OK = 0,
+    MD_ERR_ARG = -1,         /* invalid argument (NULL, NaN, out of range, bad model) */
+    MD_ERR_BOX = -2,         /* box edge < 2 rc on some axis */
+    MD_ERR_STATE = -3,       /* call out of order (e.g. no molecules set) */
+    MD_ERR_CUDA = -4,        /* a CUDA runtime call failed; see md_last_error */
+    MD_ERR_OOM = -5,         /* device allocation failed */
+    MD_ERR_NONFINITE = -6,   /* non-finite force, torque or position detected */
+    MD_ERR_OVERFLOW = -7,    /* a fixed-capacity buffer would overflow */
+    MD_ERR_TIMEOUT = -8,     /* a bounded device wait gave up */
+    MD_ERR_UNSUPPORTED = -9  /* valid input outside what this build supports */
+} md_status;
+
+/* One rigid component (molecule type), §2 "rigid rotators".  Positions are
+ * body-frame offsets from the centre of mass in the principal-axes frame
+ * (the library checks that the LJ-site masses put the centre of mass at the
+ * origin and make the inertia tensor diagonal).  Masses sit on LJ centres.
+ * Dipole and quadrupole axes are body-frame unit vectors; quadrupoles are
+ * linear, Buckingham convention (Q = Theta_zz). */
+typedef struct {
+    int32_t n_lj;
+    const double *lj_pos;    /* n_lj x 3 */
+    const int32_t *lj_type;  /* n_lj, index into md_site_types.eps/sigma */
+    const double *lj_mass;   /* n_lj */
+    int32_t n_chg;
+    const double *chg_pos;   /* n_chg x 3 */
+    const double *chg_q;     /* n_chg */
+    int32_t n_dip;
+    const double *dip_pos;   /* n_dip x 3 */
+    const double *dip_axis;  /* n_dip x 3 */
+    const double *dip_mu;    /* n_dip */
+    int32_t n_quad;
+    const double *quad_pos;  /* n_quad x 3 */
+    const double *quad_axis; /* n_quad x 3 */
+    const double *quad_Q;    /* n_quad */
+} md_component;
+
+/* LJ types (§2, Eq. 1) with Lorentz-Berthelot mixing adjusted by binary
+ * parameters: eps_ab = xi_ab sqrt(eps_a eps_b), sigma_ab = eta_ab
+ * (sigma_a + sigma_b)/2.  xi, eta are n_types x n_types, NULL = all 1. */
+typedef struct {
+    int32_t n_types;
+    const double *eps;
+    const double *sigma;
+    const double *xi;
+    const double *eta;
+    int32_t n_comp;          /* this build: exactly 1 */
+    const md_component *comp;
+} md_site_types;
+
+typedef struct {
+    double eps_rf;           /* reaction-field continuum permittivity; INFINITY allowed (§3) */
+    int32_t lj_shift;        /* 1: truncated-shifted LJ (LJTS, §2) */
+    int32_t lj_lrc;          /* 1: report the isotropic long-range correction (§3) */
+    int32_t deterministic;   /* 1: bitwise run-to-run reproducible (full-shell, no atomics) */
+    int32_t half_shell;      /* 1: Newton-3 half-shell cell pairs (§3 figure on cell enumeration) */
+} md_options;
+
+typedef struct {
+    double U_pot;            /* pair energy inside the cut-off */
+    double U_lrc;            /* long-range correction (0 unless lj_lrc) */
+    double U_rf_self;        /* reaction-field self energy, reported apart from U_pot */
+    double K_trans, K_rot;   /* kinetic energies at time t (see md_energy_virial) */
+    double W;                /* molecular virial sum_{i<j} R_ij . F_ij */
+    double W_lrc;            /* long-range virial correction */
+    double W_xx, W_yy, W_zz; /* diagonal of the molecular virial */
+    double T;                /* 2 (K_trans + K_rot) / n_dof */
+    double P;                /* (2 K_trans + W + W_lrc) / (3 V) */
+    double time;             /* simulated time since md_set_molecules */
+    int64_t step;            /* steps since md_set_molecules */
+    int64_t n_mol_pairs;     /* interacting molecule pairs (unordered) */
+    int64_t n_site_pairs;    /* interacting site pairs: n_mol_pairs * (n_lj^2 + n_el^2) */
+    int64_t n_examined;      /* distance-tested molecule pairs (unordered) */
+    int64_t n_molecules;
+} md_observables;
+
+/* Per-kernel timing gathered with CUDA events on the calling stream while
+ * profiling is enabled (md_profile). */
+typedef struct {
+    int64_t launches[8];     /* [0] integrate [1] bin [2] pack [3] force [4] kinetic [5] batch [6] adjoint [7] other */
+    double ms[8];
+} md_kernel_times;
+
+/* Creates a system: periodic box (edge lengths, each >= 2 cutoff), centre-
+ * of-mass cut-off radius (§3), site types (§2) and options.  Cells of edge
+ * >= cutoff, floor(L / cutoff) per axis (§3 linked cells).  Allocates no
+ * per-molecule memory yet.  Errors: MD_ERR_ARG, MD_ERR_BOX,
+ * MD_ERR_UNSUPPORTED (more than one component, > 8 merged sites or LJ
+ * types).  *out is set only on MD_OK. */
+md_status md_create(const double box[3], double cutoff, const md_site_types *types, const md_options *options,
+                    md_system **out);
+
+/* Replaces the molecular state with n molecules (§2 rigid rotators).
+ * comp_id may be NULL (all component 0).  r (n x 3), q (n x 4) required;
+ * v, j may be NULL (zero).  Positions are wrapped into [0, L); quaternions
+ * are renormalised.  The step counter restarts.  Asynchronous for device
+ * input; host input is copied before return.  Errors: MD_ERR_ARG (NULL
+ * r/q, n < 0, non-finite input), MD_ERR_OOM. */
+md_status md_set_molecules(md_system *sys, int64_t n, const int32_t *comp_id, const double *r, const double *v,
+                           const double *q, const double *j, int32_t on_device, void *cuda_stream);
+
+/* Rebuilds the cells (counting sort, §3) and evaluates forces, torques,
+ * energy and virial at the current configuration (§3 force calculation
+ * and summation).  Asynchronous; results stay on the device. */
+md_status md_compute_forces(md_system *sys, void *cuda_stream);
+
+/* n_steps leapfrog steps of size dt (Eqs. 2-5): half-kick/drift/rotate
+ * with the current forces, wrap, rebuild cells, recompute forces.
+ * T_target <= 0: NVE.  T_target > 0: velocity rescaling to T_target after
+ * every step (§2 NVT).  Computes forces first if they are stale.
+ * Asynchronous. */
+md_status md_step(md_system *sys, int32_t n_steps, double dt, double T_target, void *cuda_stream);
+
+/* Synchronising read-back of the observables at the current time t:
+ * U, W from the last force evaluation; K from v(t) = v(t-dt/2) + dt/2 F/m
+ * and j(t) = j(t-dt/2) + dt/2 tau with the dt of the last md_step (0 before
+ * the first step); LRC from N, V (§3).  Returns any recorded device fault. */
+md_status md_energy_virial(md_system *sys, md_observables *out);
+
+/* Copies the state back in the caller's molecule order.  Any pointer may be
+ * NULL to skip it.  Synchronising. */
+md_status md_get_molecules(md_system *sys, double *r, double *v, double *q, double *j, int32_t on_device,
+                           void *cuda_stream);
+
+/* Copies forces and torques of the last evaluation in the caller's order.
+ * Synchronising. */
+md_status md_get_forces(md_system *sys, double *F, double *tau, int32_t on_device, void *cuda_stream);
+
+/* Number of molecules currently set. */
+int64_t md_n_molecules(const md_system *sys);
+
+/* Synchronises the stream and returns any recorded device fault. */
+md_status md_sync(md_system *sys, void *cuda_stream);
+
+/* Enables (1) or disables (0) CUDA-event timing of each kernel launch on
+ * the stream the launch uses; md_kernel_times_get reads the totals. */
+md_status md_profile(md_system *sys, int32_t enable);
+md_status md_kernel_times_get(md_system *sys, md_kernel_times *out);
+
+void md_destroy(md_system *sys);
+const char *md_status_str(md_status s);
+const char *md_last_error(const md_system *sys);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -28,7 +28,7 @@ MAXT = 8
 MAXE = 16
 NOBS = 16
 OBS = {"U": 0, "W": 1, "Wxx": 2, "Wyy": 3, "Wzz": 4, "n_mol_pairs": 5, "n_site_pairs": 6,
-       "n_examined": 7, "U_lrc": 8, "W_lrc": 9, "U_rf_self": 10}
+       "n_examined": 7, "U_lrc": 8, "W_lrc": 9, "U_rf_self": 10, "abs_U": 11, "abs_W": 12}
 
 
 def build(force: bool = False) -> str:

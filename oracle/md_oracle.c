@@ -431,6 +431,7 @@ static int neighbour_cells(const cells_t *C, int64_t c, int64_t *out)
 typedef struct {
     double U, W, Wd[3];
     double nmol, nsite, nexam;
+    double absU, absW; /* sums of |u_ij| and |w_ij| over molecule pairs (error scales) */
 } sums_t;
 
 /* Full pass over molecule i's partners (each ordered pair visited from both
@@ -484,6 +485,8 @@ static void forces_for_i(const orc_model *m, const orc_setup *s, int64_t n, cons
         }
         S->U += 0.5 * o.U;
         S->W += 0.5 * o.W;
+        S->absU += 0.5 * fabs(o.U);
+        S->absW += 0.5 * fabs(o.W);
         S->nmol += 0.5;
         S->nsite += 0.5 * (double)o.nsite;
         if (gU)
@@ -537,6 +540,8 @@ static int forces_impl(const orc_model *m, const orc_setup *s, int64_t n, const 
                 S.nmol += Sl.nmol;
                 S.nsite += Sl.nsite;
                 S.nexam += Sl.nexam;
+                S.absU += Sl.absU;
+                S.absW += Sl.absW;
                 if (gU)
                     for (int p = 0; p < P; p++) {
                         gU[p] += lgU[p];
@@ -571,6 +576,8 @@ static int forces_impl(const orc_model *m, const orc_setup *s, int64_t n, const 
                 }
                 S.U += o.U;
                 S.W += o.W;
+                S.absU += fabs(o.U);
+                S.absW += fabs(o.W);
                 S.nmol += 1.0;
                 S.nsite += (double)o.nsite;
             }
@@ -591,6 +598,8 @@ static int forces_impl(const orc_model *m, const orc_setup *s, int64_t n, const 
         obs[ORC_ULRC] = lrc[0];
         obs[ORC_WLRC] = lrc[1];
         obs[ORC_URFSELF] = lrc[2];
+        obs[ORC_ABSU] = S.absU;
+        obs[ORC_ABSW] = S.absW;
     }
     return 0;
 }

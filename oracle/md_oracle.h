@@ -66,6 +66,8 @@ enum {
     ORC_NEXAM = 7,   /* examined (distance-tested) molecule pairs */
     ORC_ULRC = 8, ORC_WLRC = 9,
     ORC_URFSELF = 10,
+    ORC_ABSU = 11,   /* sum over interacting molecule pairs of |u_ij| */
+    ORC_ABSW = 12,   /* sum over interacting molecule pairs of |R_ij . F_ij| */
     ORC_NOBS = 16
 };
 

@@ -1,0 +1,765 @@
+// md_api.cu -- host side of the C ABI declared in include/md.h: argument
+// validation, compilation of the molecular model into the kernels' site
+// table, device buffers, launch sequencing of one MD step (§3: cell rebuild
+// -> force and torque calculation -> summation -> leapfrog), observables.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/md.h"
+#include "md_internal.cuh"
+
+struct PendingTiming {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+struct md_system {
+    Grid g;
+    DevModel m;
+    DevState d;
+    md_options opt;
+    int half_eff;                // half shell actually used (needs >= 3 cells per axis)
+    int n_force_blocks, n_kin_blocks;
+    long long cap;               // allocated molecules
+    bool has_mol, binned, forces_valid;
+    double dt_last, time;
+    long long step;
+    cudaStream_t last_stream;
+    // host-side model facts for the scalar terms
+    double lrc_u_coef, lrc_w_coef;  // U_LRC = coef N^2 / V (the same for W)
+    double rf_self_per_mol;
+    int n_lj, n_el;
+    char err[512];
+    // profiling
+    bool profiling;
+    std::vector<PendingTiming> pending;
+    std::vector<cudaEvent_t> pool;
+    md_kernel_times times;
+};
+
+namespace {
+
+void set_err(md_system *s, const char *fmt, ...)
+{
+    if (!s) return;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(s->err, sizeof s->err, fmt, ap);
+    va_end(ap);
+}
+
+md_status cuda_fail(md_system *s, cudaError_t e, const char *where)
+{
+    set_err(s, "%s: %s", where, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MD_ERR_OOM : MD_ERR_CUDA;
+}
+
+#define CK(call, where)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(s, e_, where); \
+    } while (0)
+
+bool finite3(const double *p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
+
+cudaEvent_t get_event(md_system *s)
+{
+    if (!s->pool.empty()) {
+        cudaEvent_t e = s->pool.back();
+        s->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+struct TimeScope {
+    md_system *s;
+    cudaStream_t st;
+    int kind;
+    cudaEvent_t a = nullptr;
+    TimeScope(md_system *s_, cudaStream_t st_, int kind_) : s(s_), st(st_), kind(kind_)
+    {
+        if (s->profiling) {
+            a = get_event(s);
+            if (a) cudaEventRecord(a, st);
+        }
+    }
+    ~TimeScope()
+    {
+        if (s->profiling && a) {
+            cudaEvent_t b = get_event(s);
+            if (b) {
+                cudaEventRecord(b, st);
+                s->pending.push_back({kind, a, b});
+            }
+        }
+    }
+};
+
+void drain_timings(md_system *s)
+{
+    for (auto &p : s->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            s->times.ms[p.kind] += ms;
+            s->times.launches[p.kind] += 1;
+        }
+        s->pool.push_back(p.a);
+        s->pool.push_back(p.b);
+    }
+    s->pending.clear();
+}
+
+// ---------------------------------------------------------- model set-up
+// Entities of the component are merged into GPU sites: an entity joins an
+// existing site at the same position when that site does not yet carry
+// its role (and, for dipoles/quadrupoles, has no axis or the same axis).
+md_status compile_model(md_system *s, const md_site_types *t, double rc, int lj_shift, double eps_rf)
+{
+    DevModel &m = s->m;
+    memset(&m, 0, sizeof m);
+    if (!t || t->n_comp != 1 || !t->comp) {
+        set_err(s, "md_site_types: exactly one component is supported (got %d)", t ? t->n_comp : -1);
+        return (t && t->n_comp > 1) ? MD_ERR_UNSUPPORTED : MD_ERR_ARG;
+    }
+    const int T = t->n_types;
+    if (T < 0 || T > MD_MAX_TYPES || (T > 0 && (!t->eps || !t->sigma))) {
+        set_err(s, "bad LJ type table (n_types=%d)", T);
+        return T > MD_MAX_TYPES ? MD_ERR_UNSUPPORTED : MD_ERR_ARG;
+    }
+    for (int a = 0; a < T; a++) {
+        if (!(std::isfinite(t->eps[a]) && t->eps[a] >= 0.0 && std::isfinite(t->sigma[a]) && t->sigma[a] > 0.0)) {
+            set_err(s, "LJ type %d: eps must be >= 0 and sigma > 0", a);
+            return MD_ERR_ARG;
+        }
+        for (int b = 0; b < T; b++) {
+            double xi = t->xi ? t->xi[a * T + b] : 1.0, eta = t->eta ? t->eta[a * T + b] : 1.0;
+            if (!(std::isfinite(xi) && xi >= 0.0 && std::isfinite(eta) && eta > 0.0)) {
+                set_err(s, "binary parameters xi/eta must be finite, xi >= 0, eta > 0");
+                return MD_ERR_ARG;
+            }
+        }
+    }
+    const md_component &c = t->comp[0];
+    if (c.n_lj < 0 || c.n_chg < 0 || c.n_dip < 0 || c.n_quad < 0 || (c.n_lj && (!c.lj_pos || !c.lj_type || !c.lj_mass)) ||
+        (c.n_chg && (!c.chg_pos || !c.chg_q)) || (c.n_dip && (!c.dip_pos || !c.dip_axis || !c.dip_mu)) ||
+        (c.n_quad && (!c.quad_pos || !c.quad_axis || !c.quad_Q))) {
+        set_err(s, "md_component: negative count or NULL array");
+        return MD_ERR_ARG;
+    }
+    struct HSite {
+        double pos[3];
+        int roles;
+        int lj_type;
+        double q, mu, Q;
+        double axis[3];
+        bool has_axis;
+    };
+    std::vector<HSite> sites;
+    auto same = [](const double *a, const double *b) {
+        return std::fabs(a[0] - b[0]) < 1e-12 && std::fabs(a[1] - b[1]) < 1e-12 && std::fabs(a[2] - b[2]) < 1e-12;
+    };
+    auto add = [&](const double *pos, int role, int ljt, double val, const double *axis) -> md_status {
+        if (!finite3(pos) || !std::isfinite(val) || (axis && !finite3(axis))) return MD_ERR_ARG;
+        double ax[3] = {0, 0, 0};
+        if (axis) {
+            double n = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
+            if (!(n > 0.0)) return MD_ERR_ARG;
+            for (int k = 0; k < 3; k++) ax[k] = axis[k] / n;
+        }
+        for (auto &h : sites) {
+            if (!same(h.pos, pos) || (h.roles & role)) continue;
+            if (axis && h.has_axis && !same(h.axis, ax)) continue;
+            h.roles |= role;
+            if (role == ROLE_LJ) h.lj_type = ljt;
+            if (role == ROLE_CHG) h.q = val;
+            if (role == ROLE_DIP) h.mu = val;
+            if (role == ROLE_QUAD) h.Q = val;
+            if (axis && !h.has_axis) {
+                memcpy(h.axis, ax, sizeof ax);
+                h.has_axis = true;
+            }
+            return MD_OK;
+        }
+        HSite h;
+        memset(&h, 0, sizeof h);
+        memcpy(h.pos, pos, sizeof h.pos);
+        h.roles = role;
+        h.lj_type = ljt;
+        if (role == ROLE_CHG) h.q = val;
+        if (role == ROLE_DIP) h.mu = val;
+        if (role == ROLE_QUAD) h.Q = val;
+        if (axis) {
+            memcpy(h.axis, ax, sizeof ax);
+            h.has_axis = true;
+        }
+        sites.push_back(h);
+        return MD_OK;
+    };
+    double mass = 0.0, com[3] = {0, 0, 0}, In[9] = {0};
+    for (int a = 0; a < c.n_lj; a++) {
+        int ty = c.lj_type[a];
+        double mm = c.lj_mass[a];
+        if (ty < 0 || ty >= T || !(std::isfinite(mm) && mm >= 0.0)) {
+            set_err(s, "LJ site %d: type out of range or bad mass", a);
+            return MD_ERR_ARG;
+        }
+        if (add(&c.lj_pos[3 * a], ROLE_LJ, ty, 0.0, nullptr) != MD_OK) {
+            set_err(s, "LJ site %d: non-finite position", a);
+            return MD_ERR_ARG;
+        }
+        const double *p = &c.lj_pos[3 * a];
+        mass += mm;
+        double p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+        for (int k = 0; k < 3; k++) com[k] += mm * p[k];
+        for (int r = 0; r < 3; r++)
+            for (int q = 0; q < 3; q++) In[3 * r + q] += mm * ((r == q ? p2 : 0.0) - p[r] * p[q]);
+    }
+    for (int a = 0; a < c.n_chg; a++)
+        if (add(&c.chg_pos[3 * a], ROLE_CHG, -1, c.chg_q[a], nullptr) != MD_OK) {
+            set_err(s, "charge %d: non-finite input", a);
+            return MD_ERR_ARG;
+        }
+    for (int a = 0; a < c.n_dip; a++)
+        if (add(&c.dip_pos[3 * a], ROLE_DIP, -1, c.dip_mu[a], &c.dip_axis[3 * a]) != MD_OK) {
+            set_err(s, "dipole %d: non-finite input or zero axis", a);
+            return MD_ERR_ARG;
+        }
+    for (int a = 0; a < c.n_quad; a++)
+        if (add(&c.quad_pos[3 * a], ROLE_QUAD, -1, c.quad_Q[a], &c.quad_axis[3 * a]) != MD_OK) {
+            set_err(s, "quadrupole %d: non-finite input or zero axis", a);
+            return MD_ERR_ARG;
+        }
+    if (sites.empty()) {
+        set_err(s, "component has no interaction sites");
+        return MD_ERR_ARG;
+    }
+    if ((int)sites.size() > MD_MAX_SITES) {
+        set_err(s, "%d merged sites exceed the supported %d", (int)sites.size(), MD_MAX_SITES);
+        return MD_ERR_UNSUPPORTED;
+    }
+    // principal-axes frame and centre of mass at the origin
+    double scale = 1e-9 * (1.0 + std::fabs(In[0]) + std::fabs(In[4]) + std::fabs(In[8]));
+    if (mass > 0.0) {
+        for (int k = 0; k < 3; k++)
+            if (std::fabs(com[k] / mass) > 1e-9) {
+                set_err(s, "LJ-site masses must put the centre of mass at the origin");
+                return MD_ERR_ARG;
+            }
+        if (std::fabs(In[1]) > scale || std::fabs(In[2]) > scale || std::fabs(In[5]) > scale) {
+            set_err(s, "body frame must be the principal-axes frame (off-diagonal inertia)");
+            return MD_ERR_ARG;
+        }
+    }
+    m.S = (int)sites.size();
+    int na = 0, rot = 0;
+    for (int a = 0; a < m.S; a++) {
+        const HSite &h = sites[a];
+        m.roles[a] = h.roles;
+        m.lj_type[a] = (h.roles & ROLE_LJ) ? h.lj_type : 0;
+        m.chg[a] = (float)h.q;
+        m.mu[a] = (float)h.mu;
+        m.Q[a] = (float)h.Q;
+        for (int k = 0; k < 3; k++) {
+            m.body[a][k] = (float)h.pos[k];
+            m.axis[a][k] = (float)h.axis[k];
+        }
+        m.axis_slot[a] = h.has_axis ? na++ : -1;
+    }
+    m.NA = na;
+    for (int a = m.S; a < MD_MAX_SITES; a++) m.axis_slot[a] = -1;
+    for (int a = 0; a < T; a++)
+        for (int b = 0; b < T; b++) {
+            double xi = t->xi ? t->xi[a * T + b] : 1.0, eta = t->eta ? t->eta[a * T + b] : 1.0;
+            double eps = xi * std::sqrt(t->eps[a] * t->eps[b]);
+            double sig = eta * 0.5 * (t->sigma[a] + t->sigma[b]);
+            m.eps4[a][b] = (float)(4.0 * eps);
+            m.eps24[a][b] = (float)(24.0 * eps);
+            m.sig2[a][b] = (float)(sig * sig);
+            double sc6 = std::pow(sig / rc, 6.0);
+            m.ushift[a][b] = lj_shift ? (float)(4.0 * eps * (sc6 * sc6 - sc6)) : 0.0f;
+        }
+    double f = std::isinf(eps_rf) ? 1.0 : 2.0 * (eps_rf - 1.0) / (2.0 * eps_rf + 1.0);
+    m.frf = (float)(f / (rc * rc * rc));
+    s->n_lj = c.n_lj;
+    s->n_el = c.n_chg + c.n_dip + c.n_quad;
+    m.site_pairs_per_mol_pair = s->n_lj * s->n_lj + s->n_el * s->n_el;
+    m.single_lj_at_com = (m.S == 1 && m.roles[0] == ROLE_LJ && sites[0].pos[0] == 0.0 && sites[0].pos[1] == 0.0 &&
+                          sites[0].pos[2] == 0.0);
+    m.mass = mass;
+    for (int k = 0; k < 3; k++) {
+        m.I[k] = In[4 * k];
+        m.Iinv[k] = In[4 * k] > 1e-12 ? 1.0 / In[4 * k] : 0.0;
+        rot += In[4 * k] > 1e-12 ? 1 : 0;
+    }
+    m.rot_dof = rot;
+    // long-range correction (§3): U_LRC = 2 pi N^2/V sum_ab 4 eps_ab [s^12/(9 rc^9) - s^6/(3 rc^3)]
+    double rc3 = rc * rc * rc, rc9 = rc3 * rc3 * rc3, cu = 0.0, cw = 0.0;
+    for (int a = 0; a < c.n_lj; a++)
+        for (int b = 0; b < c.n_lj; b++) {
+            int ta = c.lj_type[a], tb = c.lj_type[b];
+            double xi = t->xi ? t->xi[ta * T + tb] : 1.0, eta = t->eta ? t->eta[ta * T + tb] : 1.0;
+            double eps = xi * std::sqrt(t->eps[ta] * t->eps[tb]);
+            double sig = eta * 0.5 * (t->sigma[ta] + t->sigma[tb]);
+            double s6 = std::pow(sig, 6.0), s12 = s6 * s6;
+            cu += 4.0 * eps * (s12 / (9.0 * rc9) - s6 / (3.0 * rc3));
+            cw += 4.0 * eps * (4.0 * s12 / (3.0 * rc9) - 2.0 * s6 / rc3);
+        }
+    s->lrc_u_coef = 2.0 * M_PI * cu;
+    s->lrc_w_coef = 2.0 * M_PI * cw;
+    double M[3] = {0, 0, 0};
+    for (int a = 0; a < c.n_dip; a++) {
+        const double *e = &c.dip_axis[3 * a];
+        double n = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+        for (int k = 0; k < 3; k++) M[k] += c.dip_mu[a] * e[k] / n;
+    }
+    s->rf_self_per_mol = -0.5 * f * (M[0] * M[0] + M[1] * M[1] + M[2] * M[2]) / rc3;
+    return MD_OK;
+}
+
+md_status alloc_molecules(md_system *s, long long n)
+{
+    DevState &d = s->d;
+    if (n <= s->cap && d.r != nullptr) {
+        d.n = n;
+        return MD_OK;
+    }
+    double **dbl[] = {&d.r, &d.v, &d.j, &d.r2, &d.v2, &d.j2, &d.F, &d.tau};
+    for (auto p : dbl) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    cudaFree(d.q);
+    cudaFree(d.q2);
+    cudaFree(d.ids);
+    cudaFree(d.ids2);
+    cudaFree(d.cell);
+    cudaFree(d.perm);
+    cudaFree(d.perm2);
+    cudaFree(d.com);
+    cudaFree(d.geo);
+    d.q = d.q2 = nullptr;
+    d.ids = d.ids2 = d.cell = d.perm = d.perm2 = nullptr;
+    d.com = d.geo = nullptr;
+    s->cap = 0;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    cudaError_t e = cudaSuccess;
+    for (auto p : dbl)
+        if (e == cudaSuccess) e = cudaMalloc((void **)p, nn * 3 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.q, nn * 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.q2, nn * 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.ids, nn * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.ids2, nn * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.cell, nn * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.perm, nn * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.perm2, nn * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.com, nn * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.geo, nn * (size_t)(d.K > 0 ? d.K : 1) * sizeof(float4));
+    if (e != cudaSuccess) return cuda_fail(s, e, "allocating molecule buffers");
+    s->cap = n;
+    d.n = n;
+    return MD_OK;
+}
+
+void free_all(md_system *s)
+{
+    DevState &d = s->d;
+    void *ptrs[] = {d.r, d.v, d.q, d.j, d.r2, d.v2, d.q2, d.j2, d.ids, d.ids2, d.F, d.tau, d.cell, d.cell_count,
+                    d.cell_start, d.cell_fill, d.perm, d.perm2, d.com, d.geo, d.scan_tmp, d.partials,
+                    d.kin_partials, d.flags};
+    for (void *p : ptrs) cudaFree(p);
+    for (auto &p : s->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : s->pool) cudaEventDestroy(e);
+}
+
+md_status check_flags(md_system *s)
+{
+    int h[4] = {0, 0, 0, 0};
+    CK(cudaMemcpy(h, s->d.flags, sizeof h, cudaMemcpyDeviceToHost), "reading device flags");
+    if (h[FLAG_NONFINITE]) {
+        set_err(s, "non-finite force, torque or position detected on the device");
+        return MD_ERR_NONFINITE;
+    }
+    if (h[FLAG_OVERFLOW]) {
+        set_err(s, "a fixed-capacity device buffer overflowed");
+        return MD_ERR_OVERFLOW;
+    }
+    if (h[FLAG_TIMEOUT]) {
+        set_err(s, "a bounded device wait gave up");
+        return MD_ERR_TIMEOUT;
+    }
+    return MD_OK;
+}
+
+md_status do_rebuild(md_system *s, cudaStream_t st, bool need_cellid)
+{
+    TimeScope ts(s, st, 1);
+    if (need_cellid) CK(launch_cellid(s->g, s->d, st), "cell id kernel");
+    CK(launch_rebuild(s->g, s->m, s->d, st), "cell rebuild kernels");
+    s->binned = true;
+    return MD_OK;
+}
+
+md_status do_force(md_system *s, cudaStream_t st)
+{
+    TimeScope ts(s, st, 3);
+    CK(launch_force(s->g, s->m, s->d, s->half_eff, s->n_force_blocks, st), "force kernel");
+    s->forces_valid = true;
+    return MD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *md_status_str(md_status st)
+{
+    switch (st) {
+    case MD_OK: return "MD_OK";
+    case MD_ERR_ARG: return "MD_ERR_ARG: invalid argument";
+    case MD_ERR_BOX: return "MD_ERR_BOX: box edge smaller than twice the cut-off";
+    case MD_ERR_STATE: return "MD_ERR_STATE: call out of order";
+    case MD_ERR_CUDA: return "MD_ERR_CUDA: CUDA runtime error";
+    case MD_ERR_OOM: return "MD_ERR_OOM: device allocation failed";
+    case MD_ERR_NONFINITE: return "MD_ERR_NONFINITE: non-finite value detected";
+    case MD_ERR_OVERFLOW: return "MD_ERR_OVERFLOW: buffer capacity exceeded";
+    case MD_ERR_TIMEOUT: return "MD_ERR_TIMEOUT: bounded device wait gave up";
+    case MD_ERR_UNSUPPORTED: return "MD_ERR_UNSUPPORTED: input outside this build's support";
+    }
+    return "unknown md_status";
+}
+
+const char *md_last_error(const md_system *s) { return s ? s->err : "NULL handle"; }
+
+md_status md_create(const double box[3], double cutoff, const md_site_types *types, const md_options *options,
+                    md_system **out)
+{
+    if (!out || !box || !types) return MD_ERR_ARG;
+    *out = nullptr;
+    if (!(std::isfinite(cutoff) && cutoff > 0.0) || !finite3(box) || !(box[0] > 0 && box[1] > 0 && box[2] > 0))
+        return MD_ERR_ARG;
+    for (int k = 0; k < 3; k++)
+        if (box[k] < 2.0 * cutoff) return MD_ERR_BOX;
+    md_options opt = {INFINITY, 0, 0, 1, 0};
+    if (options) opt = *options;
+    if (std::isnan(opt.eps_rf) || (!std::isinf(opt.eps_rf) && opt.eps_rf < 1.0) || (std::isinf(opt.eps_rf) && opt.eps_rf < 0))
+        return MD_ERR_ARG;
+    md_system *s = new (std::nothrow) md_system();
+    if (!s) return MD_ERR_OOM;
+    s->opt = opt;
+    md_status st = compile_model(s, types, cutoff, opt.lj_shift, opt.eps_rf);
+    if (st != MD_OK) {
+        delete s;
+        return st;
+    }
+    Grid &g = s->g;
+    long long ncell = 1;
+    for (int k = 0; k < 3; k++) {
+        int nc = (int)std::floor(box[k] / (cutoff * (1.0 + 1e-9)));
+        g.nc[k] = nc < 1 ? 1 : nc;
+        g.L[k] = box[k];
+        g.ell[k] = box[k] / g.nc[k];
+        g.ellf[k] = (float)g.ell[k];
+        ncell *= g.nc[k];
+    }
+    if (ncell > (1LL << 31) - 2) {
+        delete s;
+        return MD_ERR_UNSUPPORTED;
+    }
+    g.ncell = ncell;
+    g.rc2 = cutoff * cutoff;
+    g.rc2f = (float)g.rc2;
+    g.bandf = (float)(2e-5 * g.rc2);
+    s->half_eff = (opt.half_shell && !opt.deterministic && g.nc[0] >= 3 && g.nc[1] >= 3 && g.nc[2] >= 3) ? 1 : 0;
+    s->d.K = s->m.single_lj_at_com ? 0 : s->m.S + s->m.NA;
+    long long fb = (ncell + MD_WARPS - 1) / MD_WARPS;
+    s->n_force_blocks = (int)(fb < 152 * 32 ? fb : 152 * 32);
+    s->n_kin_blocks = 152 * 4;
+    DevState &d = s->d;
+    cudaError_t e = cudaMalloc((void **)&d.cell_count, sizeof(int) * ncell);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.cell_start, sizeof(int) * (ncell + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.cell_fill, sizeof(int) * ncell);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.scan_tmp, sizeof(int) * (scan_blocks(ncell) + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.partials, sizeof(double) * P_COUNT * s->n_force_blocks);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.kin_partials, sizeof(double) * 4 * s->n_kin_blocks);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.flags, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(d.flags, 0, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(d.cell_start, 0, sizeof(int) * (ncell + 1));
+    if (e != cudaSuccess) {
+        md_status r = cuda_fail(s, e, "md_create allocations");
+        free_all(s);
+        delete s;
+        return r;
+    }
+    *out = s;
+    return MD_OK;
+}
+
+void md_destroy(md_system *s)
+{
+    if (!s) return;
+    cudaDeviceSynchronize();
+    free_all(s);
+    delete s;
+}
+
+int64_t md_n_molecules(const md_system *s) { return s ? (int64_t)s->d.n : -1; }
+
+md_status md_set_molecules(md_system *s, int64_t n, const int32_t *comp_id, const double *r, const double *v,
+                           const double *q, const double *j, int32_t on_device, void *cuda_stream)
+{
+    if (!s) return MD_ERR_ARG;
+    if (n < 0 || n > (1LL << 31) - 1 || (n > 0 && (!r || !q))) {
+        set_err(s, "md_set_molecules: n out of range or NULL r/q");
+        return MD_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (comp_id) {
+        if (on_device) {
+            set_err(s, "md_set_molecules: device comp_id is not supported (single component)");
+            return MD_ERR_UNSUPPORTED;
+        }
+        for (int64_t i = 0; i < n; i++)
+            if (comp_id[i] != 0) {
+                set_err(s, "md_set_molecules: comp_id %d out of range", comp_id[i]);
+                return MD_ERR_ARG;
+            }
+    }
+    if (!on_device) {
+        for (int64_t i = 0; i < n; i++) {
+            if (!finite3(r + 3 * i) || !finite3(q + 4 * i) || !std::isfinite(q[4 * i + 3]) ||
+                (v && !finite3(v + 3 * i)) || (j && !finite3(j + 3 * i))) {
+                set_err(s, "md_set_molecules: non-finite input for molecule %lld", (long long)i);
+                return MD_ERR_ARG;
+            }
+            double nq = q[4 * i] * q[4 * i] + q[4 * i + 1] * q[4 * i + 1] + q[4 * i + 2] * q[4 * i + 2] +
+                        q[4 * i + 3] * q[4 * i + 3];
+            if (!(nq > 0.0)) {
+                set_err(s, "md_set_molecules: zero quaternion for molecule %lld", (long long)i);
+                return MD_ERR_ARG;
+            }
+        }
+    }
+    md_status ms = alloc_molecules(s, n);
+    if (ms != MD_OK) return ms;
+    DevState &d = s->d;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    size_t b3 = sizeof(double) * 3 * (size_t)n, b4 = sizeof(double) * 4 * (size_t)n;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(d.r, r, b3, kind, st), "copy r");
+        CK(cudaMemcpyAsync(d.q, q, b4, kind, st), "copy q");
+        if (v) CK(cudaMemcpyAsync(d.v, v, b3, kind, st), "copy v");
+        else CK(cudaMemsetAsync(d.v, 0, b3, st), "zero v");
+        if (j) CK(cudaMemcpyAsync(d.j, j, b3, kind, st), "copy j");
+        else CK(cudaMemsetAsync(d.j, 0, b3, st), "zero j");
+        CK(cudaMemsetAsync(d.F, 0, b3, st), "zero F");
+        CK(cudaMemsetAsync(d.tau, 0, b3, st), "zero tau");
+    }
+    CK(launch_prepare_input(s->g, d, st), "input preparation kernel");
+    s->has_mol = true;
+    s->binned = false;
+    s->forces_valid = false;
+    s->dt_last = 0.0;
+    s->time = 0.0;
+    s->step = 0;
+    s->last_stream = st;
+    ms = do_rebuild(s, st, true);
+    if (ms != MD_OK) return ms;
+    if (!on_device) CK(cudaStreamSynchronize(st), "md_set_molecules sync");
+    return MD_OK;
+}
+
+md_status md_compute_forces(md_system *s, void *cuda_stream)
+{
+    if (!s) return MD_ERR_ARG;
+    if (!s->has_mol) {
+        set_err(s, "md_compute_forces: call md_set_molecules first");
+        return MD_ERR_STATE;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    s->last_stream = st;
+    if (!s->binned) {
+        md_status ms = do_rebuild(s, st, true);
+        if (ms != MD_OK) return ms;
+    }
+    return do_force(s, st);
+}
+
+md_status md_step(md_system *s, int32_t n_steps, double dt, double T_target, void *cuda_stream)
+{
+    if (!s) return MD_ERR_ARG;
+    if (n_steps < 0 || !std::isfinite(dt) || !(dt > 0.0) || !std::isfinite(T_target)) {
+        set_err(s, "md_step: n_steps >= 0, finite dt > 0 and finite T_target required");
+        return MD_ERR_ARG;
+    }
+    if (!s->has_mol) {
+        set_err(s, "md_step: call md_set_molecules first");
+        return MD_ERR_STATE;
+    }
+    if (T_target > 0.0) {
+        set_err(s, "md_step: velocity-rescaling NVT is not built yet; pass T_target <= 0 (NVE)");
+        return MD_ERR_UNSUPPORTED;
+    }
+    if (!(s->m.mass > 0.0)) {
+        set_err(s, "md_step: the component has no mass");
+        return MD_ERR_STATE;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    s->last_stream = st;
+    if (!s->forces_valid) {
+        md_status ms = md_compute_forces(s, st);
+        if (ms != MD_OK) return ms;
+    }
+    for (int k = 0; k < n_steps; k++) {
+        {
+            TimeScope ts(s, st, 0);
+            CK(launch_integrate(s->g, s->m, s->d, dt, st), "integrate kernel");
+        }
+        md_status ms = do_rebuild(s, st, false);
+        if (ms != MD_OK) return ms;
+        ms = do_force(s, st);
+        if (ms != MD_OK) return ms;
+        s->step++;
+        s->time += dt;
+    }
+    s->dt_last = dt;
+    return MD_OK;
+}
+
+md_status md_sync(md_system *s, void *cuda_stream)
+{
+    if (!s) return MD_ERR_ARG;
+    CK(cudaStreamSynchronize((cudaStream_t)cuda_stream), "stream synchronize");
+    if (s->profiling) drain_timings(s);
+    return check_flags(s);
+}
+
+md_status md_energy_virial(md_system *s, md_observables *out)
+{
+    if (!s || !out) return MD_ERR_ARG;
+    if (!s->forces_valid) {
+        set_err(s, "md_energy_virial: no force evaluation yet");
+        return MD_ERR_STATE;
+    }
+    cudaStream_t st = s->last_stream;
+    {
+        TimeScope ts(s, st, 4);
+        CK(launch_kinetic(s->m, s->d, 0.5 * s->dt_last, s->n_kin_blocks, st), "kinetic kernel");
+    }
+    std::vector<double> fp((size_t)P_COUNT * s->n_force_blocks), kp((size_t)4 * s->n_kin_blocks);
+    CK(cudaMemcpyAsync(fp.data(), s->d.partials, fp.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "copy partials");
+    CK(cudaMemcpyAsync(kp.data(), s->d.kin_partials, kp.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
+       "copy kinetic partials");
+    CK(cudaStreamSynchronize(st), "md_energy_virial sync");
+    if (s->profiling) drain_timings(s);
+    md_status fl = check_flags(s);
+    double acc[P_COUNT] = {0};
+    for (int b = 0; b < s->n_force_blocks; b++)
+        for (int k = 0; k < P_COUNT; k++) acc[k] += fp[(size_t)b * P_COUNT + k];
+    double kt = 0.0, kr = 0.0;
+    for (int b = 0; b < s->n_kin_blocks; b++) {
+        kt += kp[4 * b];
+        kr += kp[4 * b + 1];
+    }
+    memset(out, 0, sizeof *out);
+    const double N = (double)s->d.n, V = s->g.L[0] * s->g.L[1] * s->g.L[2];
+    out->U_pot = acc[P_U];
+    out->W = acc[P_W];
+    out->W_xx = acc[P_WXX];
+    out->W_yy = acc[P_WYY];
+    out->W_zz = acc[P_WZZ];
+    out->n_mol_pairs = (int64_t)llround(acc[P_NMOL]);
+    out->n_site_pairs = (int64_t)llround(acc[P_NSITE]);
+    out->n_examined = (int64_t)llround(acc[P_NEXAM]);
+    out->U_lrc = s->opt.lj_lrc ? s->lrc_u_coef * N * N / V : 0.0;
+    out->W_lrc = s->opt.lj_lrc ? s->lrc_w_coef * N * N / V : 0.0;
+    out->U_rf_self = s->rf_self_per_mol * N;
+    out->K_trans = kt;
+    out->K_rot = kr;
+    double dof = 3.0 * N - 3.0 + (double)s->m.rot_dof * N;
+    out->T = dof > 0 ? 2.0 * (kt + kr) / dof : 0.0;
+    out->P = (2.0 * kt + out->W + out->W_lrc) / (3.0 * V);
+    out->time = s->time;
+    out->step = s->step;
+    out->n_molecules = (int64_t)s->d.n;
+    return fl;
+}
+
+md_status md_get_molecules(md_system *s, double *r, double *v, double *q, double *j, int32_t on_device,
+                           void *cuda_stream)
+{
+    if (!s) return MD_ERR_ARG;
+    if (!s->has_mol) {
+        set_err(s, "md_get_molecules: call md_set_molecules first");
+        return MD_ERR_STATE;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    DevState &d = s->d;
+    const double *src[4] = {d.r, d.v, d.q, d.j};
+    double *dst[4] = {r, v, q, j};
+    double *tmp[4] = {d.r2, d.v2, d.q2, d.j2};
+    const int w[4] = {3, 3, 4, 3};
+    for (int k = 0; k < 4; k++) {
+        if (!dst[k] || d.n == 0) continue;
+        double *target = on_device ? dst[k] : tmp[k];
+        CK(launch_scatter_out(d, src[k], w[k], target, st), "scatter kernel");
+        if (!on_device)
+            CK(cudaMemcpyAsync(dst[k], tmp[k], sizeof(double) * w[k] * (size_t)d.n, cudaMemcpyDeviceToHost, st),
+               "copy state to host");
+    }
+    CK(cudaStreamSynchronize(st), "md_get_molecules sync");
+    return check_flags(s);
+}
+
+md_status md_get_forces(md_system *s, double *F, double *tau, int32_t on_device, void *cuda_stream)
+{
+    if (!s) return MD_ERR_ARG;
+    if (!s->forces_valid) {
+        set_err(s, "md_get_forces: no force evaluation yet");
+        return MD_ERR_STATE;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    DevState &d = s->d;
+    const double *src[2] = {d.F, d.tau};
+    double *dst[2] = {F, tau};
+    double *tmp[2] = {d.r2, d.v2};
+    for (int k = 0; k < 2; k++) {
+        if (!dst[k] || d.n == 0) continue;
+        double *target = on_device ? dst[k] : tmp[k];
+        CK(launch_scatter_out(d, src[k], 3, target, st), "scatter kernel");
+        if (!on_device)
+            CK(cudaMemcpyAsync(dst[k], tmp[k], sizeof(double) * 3 * (size_t)d.n, cudaMemcpyDeviceToHost, st),
+               "copy forces to host");
+    }
+    CK(cudaStreamSynchronize(st), "md_get_forces sync");
+    return check_flags(s);
+}
+
+md_status md_profile(md_system *s, int32_t enable)
+{
+    if (!s) return MD_ERR_ARG;
+    s->profiling = enable != 0;
+    return MD_OK;
+}
+
+md_status md_kernel_times_get(md_system *s, md_kernel_times *out)
+{
+    if (!s || !out) return MD_ERR_ARG;
+    CK(cudaStreamSynchronize(s->last_stream), "md_kernel_times_get sync");
+    drain_timings(s);
+    *out = s->times;
+    memset(&s->times, 0, sizeof s->times);
+    return MD_OK;
+}
+
+}  // extern "C"

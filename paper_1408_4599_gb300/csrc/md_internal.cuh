@@ -1,0 +1,93 @@
+// md_internal.cuh -- device-side data layout and kernel launchers of the
+// GB300 rigid multi-site MD library (arXiv 1408.4599: §2 models, §3 linked
+// cells and leapfrog).  Not part of the public ABI (see include/md.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MD_MAX_SITES 8
+#define MD_MAX_TYPES 8
+#define MD_WARPS 4          // warps per force block (one cell per warp)
+#define MD_HIT_CAP 32       // per-lane hit-list capacity before a flush
+
+// Roles a merged interaction site can carry (§2).  A site has one position
+// and at most one axis, shared by its dipole and quadrupole roles.
+enum { ROLE_LJ = 1, ROLE_CHG = 2, ROLE_DIP = 4, ROLE_QUAD = 8 };
+
+// Everything the kernels need about the (single) molecular component, as a
+// by-value kernel parameter.
+struct DevModel {
+    int S;                          // merged sites
+    int NA;                         // sites carrying an axis
+    int roles[MD_MAX_SITES];
+    int lj_type[MD_MAX_SITES];
+    int axis_slot[MD_MAX_SITES];    // index among axis-carrying sites, -1 if none
+    float chg[MD_MAX_SITES], mu[MD_MAX_SITES], Q[MD_MAX_SITES];
+    float body[MD_MAX_SITES][3];    // body-frame offsets
+    float axis[MD_MAX_SITES][3];    // body-frame unit axis
+    float eps4[MD_MAX_TYPES][MD_MAX_TYPES];   // 4 eps_ab
+    float eps24[MD_MAX_TYPES][MD_MAX_TYPES];  // 24 eps_ab
+    float sig2[MD_MAX_TYPES][MD_MAX_TYPES];   // sigma_ab^2
+    float ushift[MD_MAX_TYPES][MD_MAX_TYPES]; // LJTS shift u_ab(rc) (0 if unshifted)
+    float frf;                      // reaction-field factor / rc^3
+    int site_pairs_per_mol_pair;    // n_lj^2 + n_el^2 of the user's entities
+    int single_lj_at_com;           // 1: one LJ site at the centre of mass, nothing else
+    double mass;
+    double Iinv[3], I[3];
+    int rot_dof;                    // 0, 2 or 3
+};
+
+// Linked-cell grid (§3): n_c = floor(L / rc) cells per axis, x fastest.
+struct Grid {
+    int nc[3];
+    long long ncell;
+    double L[3];
+    double ell[3];                  // cell edge (>= rc)
+    float ellf[3];
+    double rc2;
+    float rc2f;
+    float bandf;                    // |d^2 - rc^2| below which the test is redone in FP64
+};
+
+// Device buffers of one system (storage order = sorted cell order after
+// every rebuild).
+struct DevState {
+    long long n;
+    int K;                          // float4 per molecule in geo: S + NA
+    double *r, *v, *q, *j;          // current state, n x 3 / n x 4
+    double *r2, *v2, *q2, *j2;      // reorder targets
+    int *ids, *ids2;                // caller's molecule index of each slot
+    double *F, *tau;                // n x 3, storage order
+    int *cell;                      // cell of each slot (current order)
+    int *cell_count;                // ncell
+    int *cell_start;                // ncell + 1
+    int *cell_fill;                 // ncell
+    int *perm, *perm2;              // new slot -> old slot
+    float4 *com;                    // n: centre of mass relative to its cell centre
+    float4 *geo;                    // n * K: site offsets then axes (space frame)
+    int *scan_tmp;                  // block sums of the scan
+    double *partials;               // force-kernel block partials, 8 per block
+    double *kin_partials;           // kinetic partials, 4 per block
+    int *flags;                     // [0] non-finite, [1] overflow, [2] timeout
+};
+
+// Partial-sum layout of the force kernel (per block).
+enum { P_U = 0, P_W, P_WXX, P_WYY, P_WZZ, P_NMOL, P_NSITE, P_NEXAM, P_COUNT };
+
+enum { FLAG_NONFINITE = 0, FLAG_OVERFLOW = 1, FLAG_TIMEOUT = 2 };
+
+// ------------------------------------------------------------- launchers
+// (all return cudaGetLastError() of the launch)
+cudaError_t launch_cellid(const Grid &g, DevState &d, cudaStream_t s);
+cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaStream_t s);
+cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half_shell, int n_blocks,
+                         cudaStream_t s);
+cudaError_t launch_integrate(const Grid &g, const DevModel &m, DevState &d, double dt, cudaStream_t s);
+cudaError_t launch_kinetic(const DevModel &m, DevState &d, double dt_half, int n_blocks, cudaStream_t s);
+cudaError_t launch_rescale(const DevModel &m, DevState &d, double fac_v, double fac_j, cudaStream_t s);
+cudaError_t launch_scatter_out(const DevState &d, const double *src, int width, double *dst, cudaStream_t s);
+cudaError_t launch_gather_in(DevState &d, const double *src, int width, double *dst, cudaStream_t s);
+cudaError_t launch_prepare_input(const Grid &g, DevState &d, cudaStream_t s);
+int force_blocks_default();
+int scan_blocks(long long ncell);

@@ -1,0 +1,315 @@
+"""ctypes binding of the C ABI in ``include/md.h`` (libmdgpu.so).
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels behind the ABI.  Loading fails loudly when the library is missing;
+there is no CPU fallback.  Arrays may be numpy arrays (host) or torch
+tensors (host or CUDA); CUDA streams are passed as torch streams or raw
+``cudaStream_t`` integers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmdgpu.so")
+
+MD_OK = 0
+STATUS = {0: "MD_OK", -1: "MD_ERR_ARG", -2: "MD_ERR_BOX", -3: "MD_ERR_STATE", -4: "MD_ERR_CUDA", -5: "MD_ERR_OOM",
+          -6: "MD_ERR_NONFINITE", -7: "MD_ERR_OVERFLOW", -8: "MD_ERR_TIMEOUT", -9: "MD_ERR_UNSUPPORTED"}
+KERNEL_KINDS = ("integrate", "bin", "pack", "force", "kinetic", "batch", "adjoint", "other")
+
+dp = C.POINTER(C.c_double)
+ip = C.POINTER(C.c_int32)
+
+
+class md_component(C.Structure):
+    _fields_ = [("n_lj", C.c_int32), ("lj_pos", dp), ("lj_type", ip), ("lj_mass", dp),
+                ("n_chg", C.c_int32), ("chg_pos", dp), ("chg_q", dp),
+                ("n_dip", C.c_int32), ("dip_pos", dp), ("dip_axis", dp), ("dip_mu", dp),
+                ("n_quad", C.c_int32), ("quad_pos", dp), ("quad_axis", dp), ("quad_Q", dp)]
+
+
+class md_site_types(C.Structure):
+    _fields_ = [("n_types", C.c_int32), ("eps", dp), ("sigma", dp), ("xi", dp), ("eta", dp),
+                ("n_comp", C.c_int32), ("comp", C.POINTER(md_component))]
+
+
+class md_options(C.Structure):
+    _fields_ = [("eps_rf", C.c_double), ("lj_shift", C.c_int32), ("lj_lrc", C.c_int32),
+                ("deterministic", C.c_int32), ("half_shell", C.c_int32)]
+
+
+class md_observables(C.Structure):
+    _fields_ = [("U_pot", C.c_double), ("U_lrc", C.c_double), ("U_rf_self", C.c_double),
+                ("K_trans", C.c_double), ("K_rot", C.c_double), ("W", C.c_double), ("W_lrc", C.c_double),
+                ("W_xx", C.c_double), ("W_yy", C.c_double), ("W_zz", C.c_double), ("T", C.c_double),
+                ("P", C.c_double), ("time", C.c_double), ("step", C.c_int64), ("n_mol_pairs", C.c_int64),
+                ("n_site_pairs", C.c_int64), ("n_examined", C.c_int64), ("n_molecules", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class md_kernel_times(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8)]
+
+    def as_dict(self):
+        return {k: {"launches": int(self.launches[i]), "ms": float(self.ms[i])} for i, k in enumerate(KERNEL_KINDS)}
+
+
+_lib = None
+
+# Every symbol include/md.h declares (checked by the CPU test suite).
+EXPORTS = ("md_create", "md_set_molecules", "md_compute_forces", "md_step", "md_energy_virial",
+           "md_get_molecules", "md_get_forces", "md_n_molecules", "md_sync", "md_profile", "md_kernel_times_get",
+           "md_destroy", "md_status_str", "md_last_error")
+
+
+def lib():
+    """The loaded libmdgpu.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        i32, i64 = C.c_int32, C.c_int64
+        L.md_create.argtypes = [dp, C.c_double, C.POINTER(md_site_types), C.POINTER(md_options), C.POINTER(vp)]
+        L.md_set_molecules.argtypes = [vp, i64, ip, vp, vp, vp, vp, i32, vp]
+        L.md_compute_forces.argtypes = [vp, vp]
+        L.md_step.argtypes = [vp, i32, C.c_double, C.c_double, vp]
+        L.md_energy_virial.argtypes = [vp, C.POINTER(md_observables)]
+        L.md_get_molecules.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+        L.md_get_forces.argtypes = [vp, vp, vp, i32, vp]
+        L.md_n_molecules.argtypes = [vp]
+        L.md_n_molecules.restype = i64
+        L.md_sync.argtypes = [vp, vp]
+        L.md_profile.argtypes = [vp, i32]
+        L.md_kernel_times_get.argtypes = [vp, C.POINTER(md_kernel_times)]
+        L.md_destroy.argtypes = [vp]
+        L.md_destroy.restype = None
+        L.md_status_str.argtypes = [C.c_int]
+        L.md_status_str.restype = C.c_char_p
+        L.md_last_error.argtypes = [vp]
+        L.md_last_error.restype = C.c_char_p
+        for name in ("md_create", "md_set_molecules", "md_compute_forces", "md_step", "md_energy_virial",
+                     "md_get_molecules", "md_get_forces", "md_sync", "md_profile", "md_kernel_times_get"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class MDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(code, handle=None):
+    if code != MD_OK:
+        msg = lib().md_last_error(handle).decode() if handle else lib().md_status_str(code).decode()
+        raise MDError(code, msg)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return C.c_void_p(0)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(a):
+    """(pointer, on_device, keepalive) of a numpy array or torch tensor (FP64, contiguous)."""
+    if a is None:
+        return None, 0, None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        return C.c_void_p(a.ctypes.data), 0, a
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("tensors passed to the MD ABI must be contiguous float64")
+        return C.c_void_p(a.data_ptr()), int(a.is_cuda), a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+class Model:
+    """C structs (md_site_types + md_component) for an mdgen model dict; the
+    numpy buffers are kept alive as long as this object."""
+
+    def __init__(self, md: dict):
+        self._keep = []
+        t = md_site_types()
+        eps = self._arr(md["lj_types"]["eps"])
+        sig = self._arr(md["lj_types"]["sigma"])
+        T = len(md["lj_types"]["eps"])
+        t.n_types = T
+        t.eps, t.sigma = eps, sig
+        t.xi = self._arr(np.asarray(md["xi"], float).ravel()) if md.get("xi") is not None else None
+        t.eta = self._arr(np.asarray(md["eta"], float).ravel()) if md.get("eta") is not None else None
+        c = md_component()
+        lj = md["lj"]
+        c.n_lj = len(lj)
+        c.lj_pos = self._arr([x for s in lj for x in s["pos"]])
+        c.lj_type = self._iarr([s["type"] for s in lj])
+        c.lj_mass = self._arr([s["mass"] for s in lj])
+        ch = md["charges"]
+        c.n_chg = len(ch)
+        c.chg_pos = self._arr([x for s in ch for x in s["pos"]])
+        c.chg_q = self._arr([s["q"] for s in ch])
+        dd = md["dipoles"]
+        c.n_dip = len(dd)
+        c.dip_pos = self._arr([x for s in dd for x in s["pos"]])
+        c.dip_axis = self._arr([x for s in dd for x in s["axis"]])
+        c.dip_mu = self._arr([s["mu"] for s in dd])
+        qq = md["quads"]
+        c.n_quad = len(qq)
+        c.quad_pos = self._arr([x for s in qq for x in s["pos"]])
+        c.quad_axis = self._arr([x for s in qq for x in s["axis"]])
+        c.quad_Q = self._arr([s["Q"] for s in qq])
+        self.comp = (md_component * 1)(c)
+        t.n_comp = 1
+        t.comp = self.comp
+        self.types = t
+
+    def _arr(self, v):
+        a = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+        if a.size == 0:
+            a = np.zeros(1)
+        self._keep.append(a)
+        return a.ctypes.data_as(dp)
+
+    def _iarr(self, v):
+        a = np.ascontiguousarray(np.asarray(v, dtype=np.int32))
+        if a.size == 0:
+            a = np.zeros(1, dtype=np.int32)
+        self._keep.append(a)
+        return a.ctypes.data_as(ip)
+
+
+# ------------------------------------------------------- C-ABI functions
+def md_create(box, cutoff, model: dict, eps_rf=math.inf, lj_shift=0, lj_lrc=0, deterministic=1, half_shell=0):
+    """Returns (handle, Model) -- keep the Model alive with the handle."""
+    M = Model(model)
+    b = (C.c_double * 3)(*[float(x) for x in box])
+    o = md_options(float(eps_rf), int(lj_shift), int(lj_lrc), int(deterministic), int(half_shell))
+    h = C.c_void_p()
+    _check(lib().md_create(b, float(cutoff), C.byref(M.types), C.byref(o), C.byref(h)))
+    return h, M
+
+
+def md_set_molecules(h, r, q, v=None, j=None, stream=None):
+    rp, dev, k1 = _ptr(r)
+    qp, dq, k2 = _ptr(q)
+    vp, dv, k3 = _ptr(v)
+    jp, dj, k4 = _ptr(j)
+    devs = {x for x, p in ((dev, rp), (dq, qp), (dv, vp), (dj, jp)) if p is not None}
+    if len(devs) != 1:
+        raise ValueError("all arrays must live on the same side (host or device)")
+    n = (k1.shape[0] if k1 is not None else 0)
+    _check(lib().md_set_molecules(h, n, None, rp, vp, qp, jp, dev, _stream_ptr(stream)), h)
+
+
+def md_compute_forces(h, stream=None):
+    _check(lib().md_compute_forces(h, _stream_ptr(stream)), h)
+
+
+def md_step(h, n_steps, dt, T_target=0.0, stream=None):
+    _check(lib().md_step(h, int(n_steps), float(dt), float(T_target), _stream_ptr(stream)), h)
+
+
+def md_energy_virial(h) -> dict:
+    o = md_observables()
+    _check(lib().md_energy_virial(h, C.byref(o)), h)
+    return o.as_dict()
+
+
+def md_get_molecules(h, r=None, v=None, q=None, j=None, stream=None):
+    """Fills the given arrays (host numpy or device tensors); with no
+    arrays given, returns host numpy copies of r, v, q, j."""
+    if r is None and v is None and q is None and j is None:
+        n = lib().md_n_molecules(h)
+        r, v, q, j = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 4)), np.zeros((n, 3))
+    ptrs = [_ptr(a) for a in (r, v, q, j)]
+    dev = max(p[1] for p in ptrs)
+    _check(lib().md_get_molecules(h, *[p[0] for p in ptrs], dev, _stream_ptr(stream)), h)
+    return r, v, q, j
+
+
+def md_get_forces(h, F=None, tau=None, stream=None):
+    if F is None and tau is None:
+        n = lib().md_n_molecules(h)
+        F, tau = np.zeros((n, 3)), np.zeros((n, 3))
+    pf, pt = _ptr(F), _ptr(tau)
+    dev = max(pf[1], pt[1])
+    _check(lib().md_get_forces(h, pf[0], pt[0], dev, _stream_ptr(stream)), h)
+    return F, tau
+
+
+def md_sync(h, stream=None):
+    _check(lib().md_sync(h, _stream_ptr(stream)), h)
+
+
+def md_profile(h, enable=True):
+    _check(lib().md_profile(h, int(enable)), h)
+
+
+def md_kernel_times_get(h) -> dict:
+    t = md_kernel_times()
+    _check(lib().md_kernel_times_get(h, C.byref(t)), h)
+    return t.as_dict()
+
+
+def md_destroy(h):
+    if h:
+        lib().md_destroy(h)
+
+
+class System:
+    """Owning wrapper: one md_system handle plus its model structs."""
+
+    def __init__(self, cfg: dict, deterministic=1, half_shell=0):
+        self.cfg = cfg
+        self.h, self._model = md_create(cfg["box"], cfg["rc"], cfg["model"], cfg.get("eps_rf", math.inf),
+                                        cfg.get("lj_shift", 0), cfg.get("lj_lrc", 0), deterministic, half_shell)
+
+    def set(self, r, q, v=None, j=None, stream=None):
+        md_set_molecules(self.h, r, q, v, j, stream)
+        return self
+
+    def compute_forces(self, stream=None):
+        md_compute_forces(self.h, stream)
+
+    def step(self, n_steps, dt, T_target=0.0, stream=None):
+        md_step(self.h, n_steps, dt, T_target, stream)
+
+    def observables(self):
+        return md_energy_virial(self.h)
+
+    def molecules(self, **kw):
+        return md_get_molecules(self.h, **kw)
+
+    def forces(self, **kw):
+        return md_get_forces(self.h, **kw)
+
+    def close(self):
+        if self.h:
+            md_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,97 @@
+"""C-ABI library: loads, exports every declared symbol, and validates its
+arguments on the host before touching the GPU (CPU only, no compute)."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import mdgen
+from paper_1408_4599_gb300 import md
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(md_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_library_builds_and_loads():
+    import __graft_entry__ as g
+    g.build()
+    assert os.path.exists(md.LIB_PATH)
+    md.lib()
+
+
+def test_exports_every_declared_symbol():
+    L = md.lib()
+    declared = _declared_functions()
+    assert len(declared) >= 14
+    missing = [n for n in declared if not hasattr(L, n)]
+    assert missing == []
+    assert set(md.EXPORTS) <= set(declared)
+
+
+def test_status_strings():
+    L = md.lib()
+    for code in md.STATUS:
+        assert L.md_status_str(code).decode().startswith(md.STATUS[code])
+
+
+def _create(box=(10.0, 10.0, 10.0), rc=2.5, model=None, **kw):
+    return md.md_create(box, rc, model or mdgen.model_lj(), **kw)
+
+
+def test_box_smaller_than_two_cutoffs_is_rejected():
+    with pytest.raises(md.MDError) as e:
+        _create(box=(10.0, 4.9, 10.0), rc=2.5)
+    assert e.value.code == -2
+
+
+@pytest.mark.parametrize("bad", [
+    dict(rc=-1.0), dict(rc=float("nan")), dict(box=(10.0, float("inf"), 10.0)),
+    dict(eps_rf=0.5), dict(eps_rf=float("nan")),
+])
+def test_bad_scalars_are_rejected(bad):
+    with pytest.raises(md.MDError) as e:
+        _create(**bad)
+    assert e.value.code == -1
+
+
+def test_bad_models_are_rejected():
+    m = mdgen.model_lj()
+    m["lj"][0]["type"] = 3
+    with pytest.raises(md.MDError) as e:
+        _create(model=m)
+    assert e.value.code == -1
+    m = mdgen.model_2cljq()
+    m["lj"][0]["pos"] = (0.0, 0.0, -0.3)  # centre of mass off the origin
+    with pytest.raises(md.MDError) as e:
+        _create(model=m)
+    assert e.value.code == -1
+    m = mdgen.model_lj()
+    m["lj_types"]["sigma"] = [0.0]
+    with pytest.raises(md.MDError) as e:
+        _create(model=m)
+    assert e.value.code == -1
+    m = mdgen.model_lj()
+    m["lj"] = [{"pos": (0.1 * k, 0.0, 0.0), "type": 0, "mass": 0.0} for k in range(9)]
+    with pytest.raises(md.MDError) as e:
+        _create(model=m)
+    assert e.value.code == -9  # more merged sites than supported
+
+
+def test_null_handle_calls_fail_cleanly():
+    L = md.lib()
+    assert L.md_compute_forces(None, None) == -1
+    assert L.md_step(None, 1, 0.001, 0.0, None) == -1
+    assert L.md_energy_virial(None, None) == -1
+    assert L.md_n_molecules(None) == -1
+    L.md_destroy(None)

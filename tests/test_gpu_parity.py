@@ -1,0 +1,269 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle,
+element by element on the same seeded inputs.
+
+Tolerances (FP32 site math, FP64 accumulation):
+  * forces and torques: floored relative error
+    |F - F_ref| / max(|F_ref|, 0.01 F_rms) with median <= 1e-5, max <= 1e-3;
+  * energy and virial: |dU| <= 1e-5 * sum_ij |u_ij| and |dW| <= 1e-5 *
+    sum_ij |w_ij| (an FP32 sum's error is bounded by a few ulp of the sum of
+    magnitudes of its terms);
+  * interacting / examined pair counts: exact (the pair set is decided in
+    FP64 near the cut-off);
+  * positions and quaternions after a short trajectory: 1e-5 absolute.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import mdgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1408_4599_gb300 import md  # noqa: E402
+
+LOG = os.environ.get("MD_PARITY_LOG")
+
+
+def _log(**kw):
+    if LOG:
+        with open(LOG, "a") as f:
+            f.write(json.dumps(kw) + "\n")
+
+
+def gpu_eval(cfg, deterministic=1, half=0, device=True):
+    s = md.System(cfg, deterministic=deterministic, half_shell=half)
+    if device:
+        d = torch.device("cuda:0")
+        t = {k: torch.from_numpy(np.ascontiguousarray(cfg[k])).to(d) for k in ("r", "v", "q", "j")}
+        s.set(t["r"], t["q"], t["v"], t["j"])
+    else:
+        s.set(cfg["r"], cfg["q"], cfg["v"], cfg["j"])
+    s.compute_forces()
+    F, tau = s.forces()
+    obs = s.observables()
+    s.close()
+    return F, tau, obs
+
+
+def oracle_eval(cfg, cells=True):
+    s = oracle.setup_from_config(cfg)
+    return oracle.forces(cfg["model"], s, cfg["r"], cfg["q"], use_cells=cells)
+
+
+def rel_err(A, B):
+    rms = math.sqrt(float((B ** 2).sum(axis=1).mean())) if len(B) else 1.0
+    floor = max(0.01 * rms, 1e-300)
+    return np.linalg.norm(A - B, axis=1) / np.maximum(np.linalg.norm(B, axis=1), floor)
+
+
+def check_parity(name, cfg, F, tau, obs, Fo, to, oo, exact_examined=True):
+    assert obs["n_mol_pairs"] == int(oo["n_mol_pairs"])
+    assert obs["n_site_pairs"] == int(oo["n_site_pairs"])
+    if exact_examined:
+        assert obs["n_examined"] == int(oo["n_examined"])
+    ef = rel_err(F, Fo)
+    et = rel_err(tau, to) if np.abs(to).max() > 0 else np.zeros(1)
+    dU = abs(obs["U_pot"] - oo["U"]) / max(oo["abs_U"], 1e-300)
+    dW = abs(obs["W"] - oo["W"]) / max(oo["abs_W"], 1e-300)
+    _log(case=name, n=len(F), f_med=float(np.median(ef)), f_max=float(ef.max()), t_med=float(np.median(et)),
+         t_max=float(et.max()), dU=dU, dW=dW, pairs=obs["n_mol_pairs"])
+    assert np.median(ef) <= 1e-5 and ef.max() <= 1e-3, (np.median(ef), ef.max())
+    assert np.median(et) <= 1e-5 and et.max() <= 1e-3, (np.median(et), et.max())
+    assert dU <= 1e-5, dU
+    assert dW <= 1e-5, dW
+    for k in ("Wxx", "Wyy", "Wzz"):
+        assert abs(obs["W_" + k[1:]] - oo[k]) <= 1e-5 * oo["abs_W"]
+    assert obs["U_lrc"] == pytest.approx(oo["U_lrc"], rel=1e-12, abs=1e-300)
+    assert obs["W_lrc"] == pytest.approx(oo["W_lrc"], rel=1e-12, abs=1e-300)
+
+
+CASES = {
+    "lj-4096": lambda: mdgen.config_lj_fluid(n=4096),
+    "lj-ragged-1999": lambda: mdgen.config_lj_fluid(n=1999, rho=0.45),
+    "2cljq-20000": lambda: mdgen.config_2cljq(n=20000),
+    "2cljdq-3000": lambda: mdgen.config_replica(7, 3000, 0.6, 1.0),
+    "2cljdq-smallbox-500": lambda: mdgen.config_replica(3, 500, 0.75, 1.1),
+    "2cljdq-dilute-700": lambda: mdgen.config_replica(5, 700, 0.05, 0.9),
+    "4site-6000": lambda: mdgen.config_4site(n=6000),
+    "slab-60000": lambda: mdgen.config_slab(n=60000),
+}
+
+
+@pytest.mark.parametrize("half", [0, 1])
+@pytest.mark.parametrize("name", list(CASES))
+def test_force_parity(name, half):
+    cfg = CASES[name]()
+    Fo, to, oo = oracle_eval(cfg)
+    F, tau, obs = gpu_eval(cfg, deterministic=1 - half, half=half)
+    ncs = [int(math.floor(L / (cfg["rc"] * (1 + 1e-9)))) for L in cfg["box"]]
+    check_parity(f"{name}/half{half}", cfg, F, tau, obs, Fo, to, oo, exact_examined=min(ncs) >= 3)
+
+
+def test_full_shell_is_deterministic():
+    cfg = mdgen.config_2cljq(n=8000)
+    F1, t1, o1 = gpu_eval(cfg)
+    F2, t2, o2 = gpu_eval(cfg)
+    assert np.array_equal(F1, F2) and np.array_equal(t1, t2)
+    assert o1["U_pot"] == o2["U_pot"] and o1["W"] == o2["W"]
+
+
+def test_host_and_device_inputs_agree():
+    cfg = mdgen.config_4site(n=3000)
+    F1, t1, o1 = gpu_eval(cfg, device=True)
+    F2, t2, o2 = gpu_eval(cfg, device=False)
+    assert np.array_equal(F1, F2) and np.array_equal(t1, t2)
+
+
+def _pair_cfg(X, model=None, L=12.0, rc=3.0, shift=0):
+    model = model or mdgen.model_lj()
+    c = np.array([L / 2, L / 2, L / 2])
+    r = np.array([c + np.asarray(X, float), c])
+    q = np.tile([1.0, 0, 0, 0], (2, 1))
+    return {"name": "pair", "model": model, "box": (L, L, L), "rc": rc, "lj_shift": shift, "lj_lrc": 0,
+            "eps_rf": math.inf, "dt": 0.001, "T": 1.0, "r": r, "q": q, "v": np.zeros((2, 3)), "j": np.zeros((2, 3))}
+
+
+def test_cutoff_decided_in_fp64():
+    """Pairs within 1e-9 of rc (beyond FP32 resolution) are decided exactly
+    as the FP64 definition decides them; exactly rc is outside (strict)."""
+    for frac, expect in ((1 - 1e-9, 1), (1 + 1e-9, 0), (1.0, 0), (1 - 1e-6, 1)):
+        cfg = _pair_cfg((3.0 * frac, 0, 0))
+        F, tau, obs = gpu_eval(cfg)
+        assert obs["n_mol_pairs"] == expect, frac
+    # across the periodic boundary
+    cfg = _pair_cfg((0, 0, 0), L=12.0)
+    cfg["r"] = np.array([[0.2, 6.0, 6.0], [12.0 - 2.8 * (1 + 1e-9), 6.0, 6.0]])
+    assert gpu_eval(cfg)[2]["n_mol_pairs"] == 0
+    cfg["r"] = np.array([[0.2, 6.0, 6.0], [12.0 - 2.8 * (1 - 1e-9), 6.0, 6.0]])
+    assert gpu_eval(cfg)[2]["n_mol_pairs"] == 1
+
+
+def test_two_molecule_closed_form():
+    """Eq. 1 at r = 1.5: U = 4 (1.5^-12 - 1.5^-6); F = -dU/dr along x."""
+    cfg = _pair_cfg((1.5, 0, 0))
+    F, tau, obs = gpu_eval(cfg)
+    r = 1.5
+    assert obs["U_pot"] == pytest.approx(4 * (r ** -12 - r ** -6), rel=2e-6)
+    assert F[0, 0] == pytest.approx(-4 * (-12 * r ** -13 + 6 * r ** -7), rel=2e-6)
+    assert F[1, 0] == pytest.approx(-F[0, 0], rel=1e-6)
+
+
+def test_empty_and_single_molecule():
+    cfg = mdgen.config_lj_fluid(n=64)
+    for n in (0, 1):
+        c = dict(cfg)
+        for k in ("r", "v", "q", "j"):
+            c[k] = cfg[k][:n]
+        F, tau, obs = gpu_eval(c, device=False)
+        assert obs["n_mol_pairs"] == 0 and obs["U_pot"] == 0.0 and obs["W"] == 0.0
+        assert F.shape == (n, 3) and (n == 0 or np.all(F == 0.0))
+
+
+def test_positions_outside_box_are_wrapped():
+    cfg = mdgen.config_2cljq(n=2000)
+    shifted = dict(cfg)
+    shifted["r"] = cfg["r"] + np.array(cfg["box"]) * np.array([3.0, -2.0, 1.0])
+    F1, t1, o1 = gpu_eval(cfg, device=False)
+    F2, t2, o2 = gpu_eval(shifted, device=False)
+    assert o1["n_mol_pairs"] == o2["n_mol_pairs"]
+    assert np.abs(F1 - F2).max() <= 1e-5 * np.abs(F1).max()
+
+
+def test_state_round_trip():
+    cfg = mdgen.config_4site(n=1500)
+    s = md.System(cfg)
+    s.set(cfg["r"], cfg["q"], cfg["v"], cfg["j"])
+    r, v, q, j = s.molecules()
+    s.close()
+    assert np.array_equal(v, cfg["v"]) and np.array_equal(j, cfg["j"])
+    assert np.allclose(r, np.mod(cfg["r"], np.array(cfg["box"])), atol=1e-12)
+    assert np.allclose(q, cfg["q"] / np.linalg.norm(cfg["q"], axis=1, keepdims=True), atol=1e-15)
+
+
+def test_call_order_errors():
+    cfg = mdgen.config_lj_fluid(n=100)
+    s = md.System(cfg)
+    with pytest.raises(md.MDError) as e:
+        s.compute_forces()
+    assert e.value.code == -3
+    with pytest.raises(md.MDError) as e:
+        s.step(1, 0.001)
+    assert e.value.code == -3
+    with pytest.raises(md.MDError) as e:
+        s.observables()
+    assert e.value.code == -3
+    s.close()
+
+
+def test_nonfinite_input_rejected_on_host():
+    cfg = mdgen.config_lj_fluid(n=100)
+    bad = cfg["r"].copy()
+    bad[7, 1] = np.nan
+    s = md.System(cfg)
+    with pytest.raises(md.MDError) as e:
+        s.set(bad, cfg["q"])
+    assert e.value.code == -1
+    s.close()
+
+
+# ----------------------------------------------------------- trajectories
+def _traj_compare(cfg, n_steps, tol):
+    s = md.System(cfg)
+    s.set(cfg["r"], cfg["q"], cfg["v"], cfg["j"])
+    s.step(n_steps, cfg["dt"])
+    r, v, q, j = s.molecules()
+    F, tau = s.forces()
+    obs = s.observables()
+    s.close()
+    st = oracle.step(cfg["model"], oracle.setup_from_config(cfg), {k: cfg[k] for k in ("r", "v", "q", "j")},
+                     cfg["dt"], n_steps, use_cells=True)
+    L = np.array(cfg["box"])
+    dr = r - st["r"]
+    dr -= L * np.rint(dr / L)
+    dq = np.minimum(np.abs(q - st["q"]).max(axis=1), np.abs(q + st["q"]).max(axis=1))
+    _log(case="traj/" + cfg["name"], steps=n_steps, dr=float(np.abs(dr).max()), dq=float(dq.max()),
+         dv=float(np.abs(v - st["v"]).max()), dj=float(np.abs(j - st["j"]).max()))
+    assert np.abs(dr).max() < tol
+    assert dq.max() < tol
+    assert obs["step"] == n_steps
+    kt, kr = oracle.kinetic(cfg["model"], cfg["dt"], st["v"], st["q"], st["j"], st["F"], st["tau"])
+    assert obs["K_trans"] == pytest.approx(kt, rel=1e-5)
+    assert obs["K_rot"] == pytest.approx(kr, rel=1e-5, abs=1e-12)
+
+
+def test_trajectory_lj_100_steps():
+    _traj_compare(mdgen.config_lj_fluid(n=4096), 100, 1e-5)
+
+
+def test_trajectory_2cljq_20_steps():
+    _traj_compare(mdgen.config_2cljq(n=4000), 20, 1e-5)
+
+
+def test_trajectory_4site_10_steps():
+    cfg = mdgen.config_4site(n=2000)
+    cfg["v"] *= 0.1
+    cfg["j"] *= 0.1
+    _traj_compare(cfg, 10, 1e-5)
+
+
+# -------------------------------------------------- full benchmark sizes
+@pytest.mark.parametrize("half", [0, 1])
+def test_full_size_2cljq_parity(half):
+    """The bench workload (N = 262144 2CLJQ, rc = 3), every molecule."""
+    cfg = mdgen.config_2cljq()
+    Fo, to, oo = oracle_eval(cfg)
+    F, tau, obs = gpu_eval(cfg, deterministic=1 - half, half=half)
+    check_parity(f"2cljq-262144/half{half}", cfg, F, tau, obs, Fo, to, oo)
+
+
+def test_full_size_slab_parity():
+    """Vapour-liquid slab, N = 4,194,304 single-site LJTS (uneven cells)."""
+    cfg = mdgen.config_slab()
+    Fo, to, oo = oracle_eval(cfg)
+    F, tau, obs = gpu_eval(cfg, deterministic=0, half=1)
+    check_parity("slab-4194304/half1", cfg, F, tau, obs, Fo, to, oo)
