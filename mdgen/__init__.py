@@ -171,6 +171,39 @@ def _rotate_body_to_space(q: np.ndarray, v: np.ndarray) -> np.ndarray:
     return v + w * t + np.cross(u, t)
 
 
+def site_positions(model: dict, r: np.ndarray, q: np.ndarray):
+    """Space-frame positions of every LJ centre, charge, dipole and
+    quadrupole (input preparation only) and the owning molecule index."""
+    pts = [e["pos"] for key in ("lj", "charges", "dipoles", "quads") for e in model[key]]
+    n = r.shape[0]
+    out = np.empty((n * len(pts), 3))
+    own = np.repeat(np.arange(n), len(pts))
+    for k, p in enumerate(pts):
+        out[k::len(pts)] = r + _rotate_body_to_space(q, np.tile(np.asarray(p, float), (n, 1)))
+    return out, own
+
+
+def resolve_site_overlaps(model: dict, r: np.ndarray, q: np.ndarray, box, rng: np.random.Generator,
+                          d_min: float = 0.6, max_passes: int = 100) -> np.ndarray:
+    """Re-draw the orientation of molecules whose interaction sites come
+    closer than d_min to a site of another molecule (periodic box), until
+    none do or max_passes is reached.  Returns the new quaternions."""
+    from scipy.spatial import cKDTree
+    box = np.asarray(box, float)
+    q = q.copy()
+    for _ in range(max_passes):
+        sp, own = site_positions(model, r, q)
+        tree = cKDTree(np.mod(sp, box), boxsize=box)
+        pairs = tree.query_pairs(d_min, output_type="ndarray")
+        if len(pairs):
+            pairs = pairs[own[pairs[:, 0]] != own[pairs[:, 1]]]
+        if len(pairs) == 0:
+            break
+        bad = np.unique(np.maximum(own[pairs[:, 0]], own[pairs[:, 1]]))
+        q[bad] = random_quaternions(len(bad), rng)
+    return q
+
+
 def mb_velocities(n: int, T: float, mass: float, rng: np.random.Generator) -> np.ndarray:
     """Maxwell-Boltzmann velocities at temperature T, zero total momentum,
     rescaled so that sum(m v^2) = (3n - 3) T exactly."""
@@ -246,7 +279,8 @@ def config_slab(n: int = 4194304, rho_l: float = 0.73, rho_v: float = 0.02, frac
     L_z: an fcc lattice over the slab, trimmed to count by a seeded random
     subset.  The vapour (density rho_v) fills the rest: a seeded random subset
     of a coarse simple-cubic grid with +-0.5 sigma jitter, which keeps every
-    vapour molecule at least ~2.6 sigma from the others.
+    vapour molecule at least ~2.6 sigma from the others and ~1.4 sigma from
+    the liquid faces.
     """
     rng = np.random.default_rng(seed_for(3, seed_k))
     V = n / (frac_l * rho_l + (1.0 - frac_l) * rho_v)
@@ -263,7 +297,9 @@ def config_slab(n: int = 4194304, rho_l: float = 0.73, rho_v: float = 0.02, frac
         cz += 1
     z0 = 0.5 * (Lz - t)
     liq = fcc_subset(n_l, (Lx, Lx, t), rng, jitter=0.05, cells=(cxy, cxy, cz), origin=(0.0, 0.0, z0))
-    # vapour: two regions [0, z0) and [z0 + t, Lz), total thickness Lz - t
+    # vapour: the periodic interval [z0 + t, z0 + Lz) of length Lz - t; grid
+    # layers sit half a spacing inside both ends, so no vapour molecule
+    # approaches either liquid face closer than dz/2 - 0.5
     s = (1.0 / rho_v) ** (1.0 / 3.0)
     gxy = max(1, int(math.floor(Lx / s)))
     while True:
@@ -277,10 +313,10 @@ def config_slab(n: int = 4194304, rho_l: float = 0.73, rho_v: float = 0.02, frac
     iy = (pick // gxy) % gxy
     iz = pick // (gxy * gxy)
     dz = (Lz - t) / gz
-    zz = (iz + 0.5) * dz
-    zz = np.where(zz < z0, zz, zz + t)
+    zz = np.mod(z0 + t + (iz + 0.5) * dz, Lz)
     vap = np.stack([(ix + 0.5) * (Lx / gxy), (iy + 0.5) * (Lx / gxy), zz], axis=1)
     vap += rng.uniform(-0.5, 0.5, size=vap.shape)
+    vap = np.mod(vap, np.asarray(box))
     pos = np.concatenate([liq, vap], axis=0)
     model = model_lj()
     st = _state(model, box, rng, T, pos, oriented=False)
@@ -326,13 +362,18 @@ def config_replica(k: int, n: int, rho: float, T: float, rc: float = 3.0) -> dic
 
 def config_4site(n: int = 50000, rho: float = 0.5, T: float = 1.0, rc: float = 3.0, cfg: int = 0) -> dict:
     """One configuration of the 4-site polar model (force-field gradient
-    workload): fcc subset, random orientations, seeded per configuration."""
+    workload): fcc subset, random orientations (re-drawn where sites of
+    different molecules overlap), seeded per configuration."""
     rng = np.random.default_rng(seed_for(5, cfg))
     L = (n / rho) ** (1.0 / 3.0)
     box = (L, L, L)
     model = model_4site()
     pos = fcc_subset(n, box, rng, jitter=0.05)
     st = _state(model, box, rng, T, pos)
+    # lattice start with random orientations: re-draw overlapping ones so that
+    # no two sites of different molecules are closer than 0.6 sigma
+    st["q"] = resolve_site_overlaps(model, st["r"], st["q"], box, rng, d_min=0.6)
+    st["j"] = angular_momenta(st["q"], model_principal_moments(model), T, rng)
     return {"name": f"4site-N{n}-cfg{cfg}", "model": model, "box": box, "rc": rc,
             "lj_shift": 0, "lj_lrc": 1, "eps_rf": math.inf, "dt": 0.001, "T": T, **st}
 

@@ -154,7 +154,7 @@ def test_two_molecule_closed_form():
 
 
 def test_empty_and_single_molecule():
-    cfg = mdgen.config_lj_fluid(n=64)
+    cfg = mdgen.config_lj_fluid(n=64, rho=0.05)
     for n in (0, 1):
         c = dict(cfg)
         for k in ("r", "v", "q", "j"):
