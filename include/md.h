@@ -183,6 +183,29 @@ md_status md_sync(md_system *sys, void *cuda_stream);
 md_status md_profile(md_system *sys, int32_t enable);
 md_status md_kernel_times_get(md_system *sys, md_kernel_times *out);
 
+/* Kinetic energies K_out[0] = sum 1/2 m v(t)^2 and K_out[1] = sum 1/2
+ * w.I w at time t from half-step state, exactly as md_energy_virial forms
+ * them (v(t) = v + dt/2 F/m, j(t) = j + dt/2 tau, w = I^-1 R(q)^T j(t)),
+ * but as a stand-alone call that allocates no memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate:
+ * code running inside CUDA stream capture (allocation cannot be captured),
+ * programs whose own allocator owns the device memory, and loops that must
+ * not incur the synchronisation of cudaFree.
+ *   n: molecules, at most 8,388,608 (MD_ERR_OVERFLOW beyond).
+ *   v, j, F, tau: device, n x 3 FP64; q: device, n x 4 FP64 unit
+ *   quaternions; mass > 0 and the principal moments I[3] (host, >= 0; a
+ *   zero moment contributes nothing); dt >= 0 (0 treats v, j as full-step).
+ *   K_out: device, 2 doubles, written asynchronously on cuda_stream.
+ * Scratch: a fixed 64 KiB file-scope device array, held by every GPU that
+ * loads the library until the process exits.  The first call on a device
+ * looks up the array's device address with that device current, so make
+ * that first call before any stream capture.  All calls share the scratch:
+ * calls whose work overlaps on the GPU (e.g. on different streams) race.
+ * Errors: MD_ERR_ARG, MD_ERR_OVERFLOW, MD_ERR_CUDA. */
+md_status md_kinetic_noalloc(int64_t n, const double *v, const double *q, const double *j, const double *F,
+                             const double *tau, double mass, const double I[3], double dt, double *K_out,
+                             void *cuda_stream);
+
 void md_destroy(md_system *sys);
 const char *md_status_str(md_status s);
 const char *md_last_error(const md_system *sys);

@@ -90,6 +90,8 @@ def lib():
         L.md_sync.argtypes = [vp, vp]
         L.md_profile.argtypes = [vp, i32]
         L.md_kernel_times_get.argtypes = [vp, C.POINTER(md_kernel_times)]
+        L.md_kinetic_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, C.c_double, dp, C.c_double, vp, vp]
+        L.md_kinetic_noalloc.restype = C.c_int
         L.md_destroy.argtypes = [vp]
         L.md_destroy.restype = None
         L.md_status_str.argtypes = [C.c_int]
@@ -269,6 +271,17 @@ def md_kernel_times_get(h) -> dict:
     t = md_kernel_times()
     _check(lib().md_kernel_times_get(h, C.byref(t)), h)
     return t.as_dict()
+
+
+def md_kinetic_noalloc(v, q, j, F, tau, mass, moments, dt, K_out, stream=None):
+    """K_out (device float64 tensor of 2) <- (K_trans, K_rot); allocates nothing."""
+    ptrs = [_ptr(a) for a in (v, q, j, F, tau, K_out)]
+    if min(p[1] for p in ptrs) != 1:
+        raise ValueError("md_kinetic_noalloc takes device tensors only")
+    I = (C.c_double * 3)(*[float(x) for x in moments])
+    n = ptrs[0][2].shape[0]
+    _check(lib().md_kinetic_noalloc(n, *[p[0] for p in ptrs[:5]], float(mass), I, float(dt), ptrs[5][0],
+                                    _stream_ptr(stream)))
 
 
 def md_destroy(h):
