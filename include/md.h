@@ -172,6 +172,29 @@ md_status md_get_molecules(md_system *sys, double *r, double *v, double *q, doub
  * Synchronising. */
 md_status md_get_forces(md_system *sys, double *F, double *tau, int32_t on_device, void *cuda_stream);
 
+/* Force-field parameters theta, in this order: eps_t and sigma_t of each LJ
+ * type (Eq. 1), then each charge q, each dipole moment mu and each
+ * quadrupole moment Q of the component (§2), in the md_component order.
+ * md_n_params returns their number P (-1 for a NULL handle). */
+int32_t md_n_params(const md_system *sys);
+md_status md_get_params(md_system *sys, double *theta /* P, host */);
+
+/* Replaces the parameters (same order; eps >= 0, sigma > 0, finite) and
+ * recompiles the mixing tables; geometry is unchanged.  Forces become stale.
+ * Errors: MD_ERR_ARG (wrong count or value; the old parameters stay). */
+md_status md_set_params(md_system *sys, const double *theta, int32_t n_params);
+
+/* Sensitivities for force-field fitting: d<U>/d theta and d<W>/d theta with
+ * <.> the mean over n_cfg fixed configurations, U = pair energy + LRC and
+ * W = molecular virial + LRC virial (§3).  Every pair term is recomputed
+ * (nothing is stored from a forward pass).  r_all: n_cfg x n x 3, q_all:
+ * n_cfg x n x 4 (host or device per on_device).  dU, dW: P doubles (host);
+ * means[2] = <U>, <W> (host).  Synchronising.  The system is left holding
+ * the last configuration with stale forces.  Errors: MD_ERR_ARG,
+ * MD_ERR_UNSUPPORTED (site signature without a compiled adjoint). */
+md_status md_param_grad(md_system *sys, int32_t n_cfg, int64_t n, const double *r_all, const double *q_all,
+                        int32_t on_device, double *dU, double *dW, double *means, void *cuda_stream);
+
 /* Number of molecules currently set. */
 int64_t md_n_molecules(const md_system *sys);
 

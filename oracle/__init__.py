@@ -74,7 +74,7 @@ def _lib_handle():
         lib.orc_kinetic.argtypes = [P(Model), i64, d, dp, dp, dp, dp, dp, dp]
         lib.orc_lrc.argtypes = [P(Model), P(Setup), i64, dp]
         lib.orc_n_params.argtypes = [P(Model)]
-        lib.orc_param_grad.argtypes = [P(Model), P(Setup), i32, i64, dp, dp, i32, i32, dp, dp, dp]
+        lib.orc_param_grad.argtypes = [P(Model), P(Setup), i32, i64, dp, dp, i32, i32, dp, dp, dp, dp, dp]
         lib.orc_rotmat.argtypes = [dp, dp]
         _lib = lib
     return _lib
@@ -236,9 +236,11 @@ def n_params(model: dict) -> int:
     return int(lib.orc_n_params(C.byref(M)))
 
 
-def param_grad(model: dict, setup: Setup, r_all, q_all, use_cells: bool = False, n_threads: int = 0):
+def param_grad(model: dict, setup: Setup, r_all, q_all, use_cells: bool = False, n_threads: int = 0,
+               with_abs: bool = False):
     """(dU/dtheta, dW/dtheta, <U>, <W>) averaged over the configurations in
-    r_all (n_cfg x n x 3) and q_all (n_cfg x n x 4)."""
+    r_all (n_cfg x n x 3) and q_all (n_cfg x n x 4); with_abs also returns
+    the sums of |per-pair derivative| (the error scales of the sums)."""
     lib = _lib_handle()
     r_all = _c(r_all)
     q_all = _c(q_all)
@@ -248,10 +250,14 @@ def param_grad(model: dict, setup: Setup, r_all, q_all, use_cells: bool = False,
     dU = np.zeros(P)
     dW = np.zeros(P)
     means = np.zeros(2)
+    aU = np.zeros(P)
+    aW = np.zeros(P)
     rc = lib.orc_param_grad(C.byref(M), C.byref(setup), n_cfg, n, _dp(r_all), _dp(q_all), int(use_cells),
-                            int(n_threads), _dp(dU), _dp(dW), _dp(means))
+                            int(n_threads), _dp(dU), _dp(dW), _dp(means), _dp(aU), _dp(aW))
     if rc != 0:
         raise ValueError(f"orc_param_grad failed with code {rc}")
+    if with_abs:
+        return dU, dW, float(means[0]), float(means[1]), aU, aW
     return dU, dW, float(means[0]), float(means[1])
 
 

@@ -437,7 +437,8 @@ typedef struct {
 /* Full pass over molecule i's partners (each ordered pair visited from both
  * sides); i-side force and torque, half the pair energy and virial. */
 static void forces_for_i(const orc_model *m, const orc_setup *s, int64_t n, const double *r, const double *q,
-                         const cells_t *C, int64_t i, double *Fi, double *ti, sums_t *S, double *gU, double *gW)
+                         const cells_t *C, int64_t i, double *Fi, double *ti, sums_t *S, double *gU, double *gW,
+                         double *aU, double *aW)
 {
     geom gi, gj;
     mol_geom(m, &q[4 * i], &gi);
@@ -493,12 +494,15 @@ static void forces_for_i(const orc_model *m, const orc_setup *s, int64_t n, cons
             for (int p = 0; p < P; p++) {
                 gU[p] += 0.5 * lgU[p];
                 gW[p] += 0.5 * lgW[p];
+                aU[p] += 0.5 * fabs(lgU[p]);
+                aW[p] += 0.5 * fabs(lgW[p]);
             }
     }
 }
 
 static int forces_impl(const orc_model *m, const orc_setup *s, int64_t n, const double *r, const double *q,
-                       int use_cells, int n_threads, double *F, double *tau, double *obs, double *gU, double *gW)
+                       int use_cells, int n_threads, double *F, double *tau, double *obs, double *gU, double *gW,
+                       double *aU, double *aW)
 {
     int rcode = check_setup(m, s);
     if (rcode) return rcode;
@@ -515,6 +519,8 @@ static int forces_impl(const orc_model *m, const orc_setup *s, int64_t n, const 
     if (gU) {
         memset(gU, 0, (size_t)P * sizeof(double));
         memset(gW, 0, (size_t)P * sizeof(double));
+        memset(aU, 0, (size_t)P * sizeof(double));
+        memset(aW, 0, (size_t)P * sizeof(double));
     }
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -526,12 +532,15 @@ static int forces_impl(const orc_model *m, const orc_setup *s, int64_t n, const 
         {
             sums_t Sl;
             memset(&Sl, 0, sizeof Sl);
-            double lgU[64], lgW[64];
+            double lgU[64], lgW[64], laU[64], laW[64];
             memset(lgU, 0, sizeof lgU);
             memset(lgW, 0, sizeof lgW);
+            memset(laU, 0, sizeof laU);
+            memset(laW, 0, sizeof laW);
 #pragma omp for schedule(dynamic, 64)
             for (int64_t i = 0; i < n; i++)
-                forces_for_i(m, s, n, r, q, &C, i, &F[3 * i], &tau[3 * i], &Sl, gU ? lgU : NULL, gU ? lgW : NULL);
+                forces_for_i(m, s, n, r, q, &C, i, &F[3 * i], &tau[3 * i], &Sl, gU ? lgU : NULL, gU ? lgW : NULL,
+                             laU, laW);
 #pragma omp critical
             {
                 S.U += Sl.U;
@@ -546,6 +555,8 @@ static int forces_impl(const orc_model *m, const orc_setup *s, int64_t n, const 
                     for (int p = 0; p < P; p++) {
                         gU[p] += lgU[p];
                         gW[p] += lgW[p];
+                        aU[p] += laU[p];
+                        aW[p] += laW[p];
                     }
             }
         }
@@ -566,7 +577,19 @@ static int forces_impl(const orc_model *m, const orc_setup *s, int64_t n, const 
                 mol_geom(m, &q[4 * j], &gj);
                 pair_acc o;
                 memset(&o, 0, sizeof o);
-                pair_mol(m, s, X, &gi, &gj, &o, gU, gW);
+                double pgU[64], pgW[64];
+                if (gU) {
+                    memset(pgU, 0, sizeof pgU);
+                    memset(pgW, 0, sizeof pgW);
+                }
+                pair_mol(m, s, X, &gi, &gj, &o, gU ? pgU : NULL, gU ? pgW : NULL);
+                if (gU)
+                    for (int p = 0; p < P; p++) {
+                        gU[p] += pgU[p];
+                        gW[p] += pgW[p];
+                        aU[p] += fabs(pgU[p]);
+                        aW[p] += fabs(pgW[p]);
+                    }
                 for (int k = 0; k < 3; k++) {
                     F[3 * i + k] += o.Fi[k];
                     F[3 * j + k] -= o.Fi[k];
@@ -607,7 +630,7 @@ static int forces_impl(const orc_model *m, const orc_setup *s, int64_t n, const 
 int orc_forces(const orc_model *m, const orc_setup *s, int64_t n, const double *r, const double *q, int use_cells,
                int n_threads, double *F, double *tau, double *obs)
 {
-    return forces_impl(m, s, n, r, q, use_cells, n_threads, F, tau, obs, NULL, NULL);
+    return forces_impl(m, s, n, r, q, use_cells, n_threads, F, tau, obs, NULL, NULL, NULL, NULL);
 }
 
 /* Exact force and torque on selected molecules only (linked cells), for
@@ -630,7 +653,7 @@ int orc_forces_subset(const orc_model *m, const orc_setup *s, int64_t n, const d
     for (int64_t t = 0; t < n_sel; t++) {
         sums_t Sl;
         memset(&Sl, 0, sizeof Sl);
-        forces_for_i(m, s, n, r, q, &C, sel[t], &F[3 * t], &tau[3 * t], &Sl, NULL, NULL);
+        forces_for_i(m, s, n, r, q, &C, sel[t], &F[3 * t], &tau[3 * t], &Sl, NULL, NULL, NULL, NULL);
     }
     cells_free(&C);
     return 0;
@@ -749,7 +772,7 @@ int orc_step(const orc_model *m, const orc_setup *s, int64_t n, double dt, int n
             for (int k = 0; k < 4; k++) qi[k] += dt * qd[k];
             normalise4(qi);
         }
-        int rcode = forces_impl(m, s, n, r, q, use_cells, n_threads, F, tau, obs, NULL, NULL);
+        int rcode = forces_impl(m, s, n, r, q, use_cells, n_threads, F, tau, obs, NULL, NULL, NULL, NULL);
         if (rcode) return rcode;
     }
     return 0;
@@ -783,9 +806,12 @@ int orc_kinetic(const orc_model *m, int64_t n, double dt, const double *v, const
  * d<U>/d theta and d<W>/d theta averaged over n_cfg fixed configurations,
  * theta = (eps_t for each LJ type, sigma_t for each LJ type, each charge q,
  * each dipole mu, each quadrupole Q).  U and W include the long-range
- * correction when it is enabled.  means[0] = <U>, means[1] = <W>. */
+ * correction when it is enabled.  means[0] = <U>, means[1] = <W>.
+ * absU/absW: mean over configurations of sum over molecule pairs of
+ * |d u_ij / d theta| and |d w_ij / d theta| (the error scale of a sum). */
 int orc_param_grad(const orc_model *m, const orc_setup *s, int n_cfg, int64_t n, const double *r_all,
-                   const double *q_all, int use_cells, int n_threads, double *dU, double *dW, double *means)
+                   const double *q_all, int use_cells, int n_threads, double *dU, double *dW, double *means,
+                   double *absU, double *absW)
 {
     int P = orc_n_params(m);
     if (P > 64) return -1;
@@ -793,13 +819,15 @@ int orc_param_grad(const orc_model *m, const orc_setup *s, int n_cfg, int64_t n,
     double *F = (double *)malloc((size_t)(n > 0 ? n : 1) * 3 * sizeof(double));
     double *tau = (double *)malloc((size_t)(n > 0 ? n : 1) * 3 * sizeof(double));
     if (!F || !tau) return -5;
-    double gU[64], gW[64], obs[ORC_NOBS];
+    double gU[64], gW[64], aU[64], aW[64], obs[ORC_NOBS];
     memset(dU, 0, (size_t)P * sizeof(double));
     memset(dW, 0, (size_t)P * sizeof(double));
+    memset(absU, 0, (size_t)P * sizeof(double));
+    memset(absW, 0, (size_t)P * sizeof(double));
     means[0] = means[1] = 0.0;
     for (int c = 0; c < n_cfg; c++) {
         int rcode = forces_impl(m, s, n, &r_all[(size_t)c * n * 3], &q_all[(size_t)c * n * 4], use_cells, n_threads,
-                                F, tau, obs, gU, gW);
+                                F, tau, obs, gU, gW, aU, aW);
         if (rcode) {
             free(F);
             free(tau);
@@ -808,6 +836,8 @@ int orc_param_grad(const orc_model *m, const orc_setup *s, int n_cfg, int64_t n,
         for (int p = 0; p < P; p++) {
             dU[p] += gU[p] / n_cfg;
             dW[p] += gW[p] / n_cfg;
+            absU[p] += aU[p] / n_cfg;
+            absW[p] += aW[p] / n_cfg;
         }
         means[0] += (obs[ORC_U] + obs[ORC_ULRC]) / n_cfg;
         means[1] += (obs[ORC_W] + obs[ORC_WLRC]) / n_cfg;

@@ -82,7 +82,8 @@ int orc_kinetic(const orc_model *m, int64_t n, double dt, const double *v, const
 int orc_lrc(const orc_model *m, const orc_setup *s, int64_t n, double *out);
 int orc_n_params(const orc_model *m);
 int orc_param_grad(const orc_model *m, const orc_setup *s, int n_cfg, int64_t n, const double *r_all,
-                   const double *q_all, int use_cells, int n_threads, double *dU, double *dW, double *means);
+                   const double *q_all, int use_cells, int n_threads, double *dU, double *dW, double *means,
+                   double *absU, double *absW);
 int orc_rotmat(const double *q, double *R);
 
 #endif

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -16,6 +17,26 @@
 struct PendingTiming {
     int kind;
     cudaEvent_t a, b;
+};
+
+// Editable copy of the caller's model (parameters can be replaced later).
+struct HostModel {
+    int T = 0;
+    std::vector<double> eps, sigma, xi, eta;
+    int n_lj = 0, n_chg = 0, n_dip = 0, n_quad = 0;
+    std::vector<double> lj_pos, lj_mass, chg_pos, chg_q, dip_pos, dip_axis, dip_mu, quad_pos, quad_axis, quad_Q;
+    std::vector<int32_t> lj_type;
+    bool has_xi = false, has_eta = false;
+    md_component comp;
+    md_site_types types;
+    void view()
+    {
+        comp = md_component{n_lj, lj_pos.data(), lj_type.data(), lj_mass.data(), n_chg, chg_pos.data(), chg_q.data(),
+                            n_dip, dip_pos.data(), dip_axis.data(), dip_mu.data(), n_quad, quad_pos.data(),
+                            quad_axis.data(), quad_Q.data()};
+        types = md_site_types{T, eps.data(), sigma.data(), has_xi ? xi.data() : nullptr,
+                              has_eta ? eta.data() : nullptr, 1, &comp};
+    }
 };
 
 struct md_system {
@@ -34,6 +55,14 @@ struct md_system {
     double lrc_u_coef, lrc_w_coef;  // U_LRC = coef N^2 / V (the same for W)
     double rf_self_per_mol;
     int n_lj, n_el;
+    HostModel hm;
+    double rc;
+    // electrostatic entities in the adjoint kernel's order (site, then charge/dipole/quadrupole):
+    // parameter index and strength; LJ sites in site order: type
+    std::vector<int> ent_param, lj_site_type;
+    std::vector<double> ent_strength;
+    double *adj_partials = nullptr;
+    int adj_nacc = 0;
     char err[512];
     // profiling
     bool profiling;
@@ -166,6 +195,9 @@ md_status compile_model(md_system *s, const md_site_types *t, double rc, int lj_
     auto same = [](const double *a, const double *b) {
         return std::fabs(a[0] - b[0]) < 1e-12 && std::fabs(a[1] - b[1]) < 1e-12 && std::fabs(a[2] - b[2]) < 1e-12;
     };
+    std::vector<std::vector<int>> site_param(MD_MAX_SITES + 8, std::vector<int>(3, -1));
+    int cur_param = -1;
+    auto role_idx = [](int role) { return role == ROLE_CHG ? 0 : (role == ROLE_DIP ? 1 : 2); };
     auto add = [&](const double *pos, int role, int ljt, double val, const double *axis) -> md_status {
         if (!finite3(pos) || !std::isfinite(val) || (axis && !finite3(axis))) return MD_ERR_ARG;
         double ax[3] = {0, 0, 0};
@@ -186,6 +218,8 @@ md_status compile_model(md_system *s, const md_site_types *t, double rc, int lj_
                 memcpy(h.axis, ax, sizeof ax);
                 h.has_axis = true;
             }
+            size_t si = (size_t)(&h - sites.data());
+            if (role != ROLE_LJ && si < site_param.size()) site_param[si][role_idx(role)] = cur_param;
             return MD_OK;
         }
         HSite h;
@@ -201,6 +235,8 @@ md_status compile_model(md_system *s, const md_site_types *t, double rc, int lj_
             h.has_axis = true;
         }
         sites.push_back(h);
+        size_t si = sites.size() - 1;
+        if (role != ROLE_LJ && si < site_param.size()) site_param[si][role_idx(role)] = cur_param;
         return MD_OK;
     };
     double mass = 0.0, com[3] = {0, 0, 0}, In[9] = {0};
@@ -223,17 +259,19 @@ md_status compile_model(md_system *s, const md_site_types *t, double rc, int lj_
             for (int q = 0; q < 3; q++) In[3 * r + q] += mm * ((r == q ? p2 : 0.0) - p[r] * p[q]);
     }
     for (int a = 0; a < c.n_chg; a++)
-        if (add(&c.chg_pos[3 * a], ROLE_CHG, -1, c.chg_q[a], nullptr) != MD_OK) {
+        if ((cur_param = 2 * T + a, add(&c.chg_pos[3 * a], ROLE_CHG, -1, c.chg_q[a], nullptr)) != MD_OK) {
             set_err(s, "charge %d: non-finite input", a);
             return MD_ERR_ARG;
         }
     for (int a = 0; a < c.n_dip; a++)
-        if (add(&c.dip_pos[3 * a], ROLE_DIP, -1, c.dip_mu[a], &c.dip_axis[3 * a]) != MD_OK) {
+        if ((cur_param = 2 * T + c.n_chg + a, add(&c.dip_pos[3 * a], ROLE_DIP, -1, c.dip_mu[a], &c.dip_axis[3 * a])) !=
+            MD_OK) {
             set_err(s, "dipole %d: non-finite input or zero axis", a);
             return MD_ERR_ARG;
         }
     for (int a = 0; a < c.n_quad; a++)
-        if (add(&c.quad_pos[3 * a], ROLE_QUAD, -1, c.quad_Q[a], &c.quad_axis[3 * a]) != MD_OK) {
+        if ((cur_param = 2 * T + c.n_chg + c.n_dip + a,
+             add(&c.quad_pos[3 * a], ROLE_QUAD, -1, c.quad_Q[a], &c.quad_axis[3 * a])) != MD_OK) {
             set_err(s, "quadrupole %d: non-finite input or zero axis", a);
             return MD_ERR_ARG;
         }
@@ -285,7 +323,22 @@ md_status compile_model(md_system *s, const md_site_types *t, double rc, int lj_
             m.sig2[a][b] = (float)(sig * sig);
             double sc6 = std::pow(sig / rc, 6.0);
             m.ushift[a][b] = lj_shift ? (float)(4.0 * eps * (sc6 * sc6 - sc6)) : 0.0f;
+            m.isig[a][b] = (float)(1.0 / sig);
+            m.ushift_e[a][b] = lj_shift ? (float)(4.0 * (sc6 * sc6 - sc6)) : 0.0f;
+            m.dshift_s[a][b] = lj_shift ? (float)(4.0 / sig * (12.0 * sc6 * sc6 - 6.0 * sc6)) : 0.0f;
         }
+    s->ent_param.clear();
+    s->ent_strength.clear();
+    s->lj_site_type.clear();
+    for (int a = 0; a < m.S; a++) {
+        const int order[3] = {ROLE_CHG, ROLE_DIP, ROLE_QUAD};
+        for (int t = 0; t < 3; t++)
+            if (sites[a].roles & order[t]) {
+                s->ent_param.push_back(site_param[a][t]);
+                s->ent_strength.push_back(t == 0 ? sites[a].q : (t == 1 ? sites[a].mu : sites[a].Q));
+            }
+        if (sites[a].roles & ROLE_LJ) s->lj_site_type.push_back(sites[a].lj_type);
+    }
     double f = std::isinf(eps_rf) ? 1.0 : 2.0 * (eps_rf - 1.0) / (2.0 * eps_rf + 1.0);
     m.frf = (float)(f / (rc * rc * rc));
     s->n_lj = c.n_lj;
@@ -324,6 +377,53 @@ md_status compile_model(md_system *s, const md_site_types *t, double rc, int lj_
     return MD_OK;
 }
 
+// Keeps an editable copy of the caller's model (md_set_params replaces its
+// parameters and recompiles).
+md_status copy_model(md_system *s, const md_site_types *t)
+{
+    if (!t || t->n_comp != 1 || !t->comp) {
+        set_err(s, "md_site_types: exactly one component is supported (got %d)", t ? t->n_comp : -1);
+        return (t && t->n_comp > 1) ? MD_ERR_UNSUPPORTED : MD_ERR_ARG;
+    }
+    const md_component &c = t->comp[0];
+    if (t->n_types < 0 || t->n_types > MD_MAX_TYPES || (t->n_types > 0 && (!t->eps || !t->sigma)) || c.n_lj < 0 ||
+        c.n_chg < 0 || c.n_dip < 0 || c.n_quad < 0 || (c.n_lj && (!c.lj_pos || !c.lj_type || !c.lj_mass)) ||
+        (c.n_chg && (!c.chg_pos || !c.chg_q)) || (c.n_dip && (!c.dip_pos || !c.dip_axis || !c.dip_mu)) ||
+        (c.n_quad && (!c.quad_pos || !c.quad_axis || !c.quad_Q))) {
+        set_err(s, "md_site_types / md_component: bad count or NULL array");
+        return t->n_types > MD_MAX_TYPES ? MD_ERR_UNSUPPORTED : MD_ERR_ARG;
+    }
+    HostModel &h = s->hm;
+    const int T = t->n_types;
+    h.T = T;
+    h.eps.assign(t->eps, t->eps + T);
+    h.sigma.assign(t->sigma, t->sigma + T);
+    h.has_xi = t->xi != nullptr;
+    h.has_eta = t->eta != nullptr;
+    h.xi.assign(T * T, 1.0);
+    h.eta.assign(T * T, 1.0);
+    if (t->xi) h.xi.assign(t->xi, t->xi + T * T);
+    if (t->eta) h.eta.assign(t->eta, t->eta + T * T);
+    h.n_lj = c.n_lj;
+    h.n_chg = c.n_chg;
+    h.n_dip = c.n_dip;
+    h.n_quad = c.n_quad;
+    auto cp = [](std::vector<double> &v, const double *p, int n) { v.assign(p ? p : nullptr, p ? p + n : nullptr); };
+    cp(h.lj_pos, c.lj_pos, 3 * c.n_lj);
+    cp(h.lj_mass, c.lj_mass, c.n_lj);
+    h.lj_type.assign(c.lj_type ? c.lj_type : nullptr, c.lj_type ? c.lj_type + c.n_lj : nullptr);
+    cp(h.chg_pos, c.chg_pos, 3 * c.n_chg);
+    cp(h.chg_q, c.chg_q, c.n_chg);
+    cp(h.dip_pos, c.dip_pos, 3 * c.n_dip);
+    cp(h.dip_axis, c.dip_axis, 3 * c.n_dip);
+    cp(h.dip_mu, c.dip_mu, c.n_dip);
+    cp(h.quad_pos, c.quad_pos, 3 * c.n_quad);
+    cp(h.quad_axis, c.quad_axis, 3 * c.n_quad);
+    cp(h.quad_Q, c.quad_Q, c.n_quad);
+    h.view();
+    return MD_OK;
+}
+
 md_status alloc_molecules(md_system *s, long long n)
 {
     DevState &d = s->d;
@@ -345,6 +445,8 @@ md_status alloc_molecules(md_system *s, long long n)
     cudaFree(d.perm2);
     cudaFree(d.com);
     cudaFree(d.geo);
+    cudaFree(d.facc);
+    d.facc = nullptr;
     d.q = d.q2 = nullptr;
     d.ids = d.ids2 = d.cell = d.perm = d.perm2 = nullptr;
     d.com = d.geo = nullptr;
@@ -362,6 +464,7 @@ md_status alloc_molecules(md_system *s, long long n)
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.perm2, nn * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.com, nn * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.geo, nn * (size_t)(d.K > 0 ? d.K : 1) * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.facc, nn * 6 * sizeof(float));
     if (e != cudaSuccess) return cuda_fail(s, e, "allocating molecule buffers");
     s->cap = n;
     d.n = n;
@@ -373,7 +476,7 @@ void free_all(md_system *s)
     DevState &d = s->d;
     void *ptrs[] = {d.r, d.v, d.q, d.j, d.r2, d.v2, d.q2, d.j2, d.ids, d.ids2, d.F, d.tau, d.cell, d.cell_count,
                     d.cell_start, d.cell_fill, d.perm, d.perm2, d.com, d.geo, d.scan_tmp, d.partials,
-                    d.kin_partials, d.flags};
+                    d.kin_partials, d.flags, d.facc, s->adj_partials};
     for (void *p : ptrs) cudaFree(p);
     for (auto &p : s->pending) {
         cudaEventDestroy(p.a);
@@ -457,7 +560,9 @@ md_status md_create(const double box[3], double cutoff, const md_site_types *typ
     md_system *s = new (std::nothrow) md_system();
     if (!s) return MD_ERR_OOM;
     s->opt = opt;
-    md_status st = compile_model(s, types, cutoff, opt.lj_shift, opt.eps_rf);
+    s->rc = cutoff;
+    md_status st = copy_model(s, types);
+    if (st == MD_OK) st = compile_model(s, &s->hm.types, cutoff, opt.lj_shift, opt.eps_rf);
     if (st != MD_OK) {
         delete s;
         return st;
@@ -482,8 +587,9 @@ md_status md_create(const double box[3], double cutoff, const md_site_types *typ
     g.bandf = (float)(2e-5 * g.rc2);
     s->half_eff = (opt.half_shell && !opt.deterministic && g.nc[0] >= 3 && g.nc[1] >= 3 && g.nc[2] >= 3) ? 1 : 0;
     s->d.K = s->m.single_lj_at_com ? 0 : s->m.S + s->m.NA;
+
     long long fb = (ncell + MD_WARPS - 1) / MD_WARPS;
-    s->n_force_blocks = (int)(fb < 152 * 32 ? fb : 152 * 32);
+    s->n_force_blocks = (int)(fb < 152 * 4 ? fb : 152 * 4);  // persistent: grid-stride over cells
     s->n_kin_blocks = 152 * 4;
     DevState &d = s->d;
     cudaError_t e = cudaMalloc((void **)&d.cell_count, sizeof(int) * ncell);
@@ -743,6 +849,155 @@ md_status md_get_forces(md_system *s, double *F, double *tau, int32_t on_device,
     }
     CK(cudaStreamSynchronize(st), "md_get_forces sync");
     return check_flags(s);
+}
+
+int32_t md_n_params(const md_system *s)
+{
+    if (!s) return -1;
+    const HostModel &h = s->hm;
+    return 2 * h.T + h.n_chg + h.n_dip + h.n_quad;
+}
+
+md_status md_get_params(md_system *s, double *theta)
+{
+    if (!s || !theta) return MD_ERR_ARG;
+    const HostModel &h = s->hm;
+    int k = 0;
+    for (int t = 0; t < h.T; t++) theta[k++] = h.eps[t];
+    for (int t = 0; t < h.T; t++) theta[k++] = h.sigma[t];
+    for (int a = 0; a < h.n_chg; a++) theta[k++] = h.chg_q[a];
+    for (int a = 0; a < h.n_dip; a++) theta[k++] = h.dip_mu[a];
+    for (int a = 0; a < h.n_quad; a++) theta[k++] = h.quad_Q[a];
+    return MD_OK;
+}
+
+md_status md_set_params(md_system *s, const double *theta, int32_t n_params)
+{
+    if (!s || !theta) return MD_ERR_ARG;
+    if (n_params != md_n_params(s)) {
+        set_err(s, "md_set_params: expected %d parameters, got %d", md_n_params(s), n_params);
+        return MD_ERR_ARG;
+    }
+    HostModel h = s->hm;
+    int k = 0;
+    for (int t = 0; t < h.T; t++) h.eps[t] = theta[k++];
+    for (int t = 0; t < h.T; t++) h.sigma[t] = theta[k++];
+    for (int a = 0; a < h.n_chg; a++) h.chg_q[a] = theta[k++];
+    for (int a = 0; a < h.n_dip; a++) h.dip_mu[a] = theta[k++];
+    for (int a = 0; a < h.n_quad; a++) h.quad_Q[a] = theta[k++];
+    h.view();
+    DevModel keep = s->m;
+    md_status st = compile_model(s, &h.types, s->rc, s->opt.lj_shift, s->opt.eps_rf);
+    if (st != MD_OK) {
+        s->m = keep;
+        compile_model(s, &s->hm.types, s->rc, s->opt.lj_shift, s->opt.eps_rf);
+        return st;
+    }
+    s->hm = h;
+    s->hm.view();
+    s->forces_valid = false;
+    return MD_OK;
+}
+
+md_status md_param_grad(md_system *s, int32_t n_cfg, int64_t n, const double *r_all, const double *q_all,
+                        int32_t on_device, double *dU, double *dW, double *means, void *cuda_stream)
+{
+    if (!s || n_cfg < 1 || n < 0 || (n > 0 && (!r_all || !q_all)) || !dU || !dW || !means) return MD_ERR_ARG;
+    const int nacc = adjoint_nacc(s->m);
+    if (nacc < 0) {
+        set_err(s, "md_param_grad: the adjoint kernel is compiled for the built-in site signatures only");
+        return MD_ERR_UNSUPPORTED;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (s->adj_nacc != nacc) {
+        cudaFree(s->adj_partials);
+        s->adj_partials = nullptr;
+        s->adj_nacc = 0;
+        CK(cudaMalloc((void **)&s->adj_partials, sizeof(double) * (size_t)nacc * s->n_force_blocks),
+           "allocating adjoint partials");
+        s->adj_nacc = nacc;
+    }
+    const int half = (s->g.nc[0] >= 3 && s->g.nc[1] >= 3 && s->g.nc[2] >= 3) ? 1 : 0;
+    std::vector<double> tot(nacc, 0.0), part((size_t)nacc * s->n_force_blocks);
+    for (int c = 0; c < n_cfg; c++) {
+        md_status ms = md_set_molecules(s, n, nullptr, r_all + (size_t)c * n * 3, nullptr, q_all + (size_t)c * n * 4,
+                                        nullptr, on_device, cuda_stream);
+        if (ms != MD_OK) return ms;
+        {
+            TimeScope ts(s, st, 6);
+            CK(launch_adjoint(s->g, s->m, s->d, half, s->n_force_blocks, s->adj_partials, nacc, st), "adjoint kernel");
+        }
+        CK(cudaMemcpyAsync(part.data(), s->adj_partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
+           "copy adjoint partials");
+        CK(cudaStreamSynchronize(st), "md_param_grad sync");
+        for (int b = 0; b < s->n_force_blocks; b++)
+            for (int q = 0; q < nacc; q++) tot[q] += part[(size_t)b * nacc + q];
+    }
+    if (s->profiling) drain_timings(s);
+    for (auto &v : tot) v /= (double)n_cfg;
+    const HostModel &h = s->hm;
+    const int T = h.T, P = md_n_params(s);
+    for (int p = 0; p < P; p++) dU[p] = dW[p] = 0.0;
+    auto mix = [&](int ta, int tb, double &eps, double &sig, double &eta) {
+        eps = h.xi[ta * T + tb] * std::sqrt(h.eps[ta] * h.eps[tb]);
+        eta = h.eta[ta * T + tb];
+        sig = eta * 0.5 * (h.sigma[ta] + h.sigma[tb]);
+    };
+    // chain rule through Lorentz-Berthelot: d eps_ab / d eps_t = eps_ab (n_t) / (2 eps_t),
+    // d sigma_ab / d sigma_t = eta_ab n_t / 2, n_t = [a is t] + [b is t]
+    auto lj_chain = [&](int ta, int tb, double su_e, double sw_e, double su_s, double sw_s) {
+        double eps, sig, eta;
+        mix(ta, tb, eps, sig, eta);
+        for (int t = 0; t < T; t++) {
+            const double nt = (double)((ta == t) + (tb == t));
+            if (nt == 0.0) continue;
+            const double de = h.eps[t] > 0.0 ? eps * nt / (2.0 * h.eps[t]) : 0.0;
+            const double ds = eta * nt * 0.5;
+            dU[t] += su_e * de;
+            dW[t] += sw_e * de;
+            dU[T + t] += su_s * ds;
+            dW[T + t] += sw_s * ds;
+        }
+    };
+    const int NLJ = (int)s->lj_site_type.size(), NE = (int)s->ent_param.size();
+    for (int a = 0; a < NLJ; a++)
+        for (int b = 0; b < NLJ; b++) {
+            const double *v = &tot[4 * (a * NLJ + b)];
+            lj_chain(s->lj_site_type[a], s->lj_site_type[b], v[0], v[1], v[2], v[3]);
+        }
+    // bilinear in the strengths
+    for (int ea = 0; ea < NE; ea++)
+        for (int eb = 0; eb < NE; eb++) {
+            const double U1 = tot[4 * NLJ * NLJ + 2 * (ea * NE + eb)], W1 = tot[4 * NLJ * NLJ + 2 * (ea * NE + eb) + 1];
+            dU[s->ent_param[ea]] += s->ent_strength[eb] * U1;
+            dW[s->ent_param[ea]] += s->ent_strength[eb] * W1;
+            dU[s->ent_param[eb]] += s->ent_strength[ea] * U1;
+            dW[s->ent_param[eb]] += s->ent_strength[ea] * W1;
+        }
+    double U = tot[nacc - 2], W = tot[nacc - 1];
+    if (s->opt.lj_lrc) {
+        // isotropic tail (§3) per LJ centre pair and its parameter derivatives
+        const double V = s->g.L[0] * s->g.L[1] * s->g.L[2];
+        const double rc = s->rc, rc3 = rc * rc * rc, rc9 = rc3 * rc3 * rc3;
+        const double pre = 2.0 * M_PI * (double)n * (double)n / V;
+        for (int a = 0; a < h.n_lj; a++)
+            for (int b = 0; b < h.n_lj; b++) {
+                const int ta = h.lj_type[a], tb = h.lj_type[b];
+                double eps, sig, eta;
+                mix(ta, tb, eps, sig, eta);
+                const double s5 = std::pow(sig, 5.0), s6 = s5 * sig, s11 = s6 * s5, s12 = s6 * s6;
+                const double uL = 4.0 * (s12 / (9.0 * rc9) - s6 / (3.0 * rc3));
+                const double wL = 4.0 * (4.0 * s12 / (3.0 * rc9) - 2.0 * s6 / rc3);
+                U += pre * eps * uL;
+                W += pre * eps * wL;
+                lj_chain(ta, tb, pre * uL, pre * wL, pre * 4.0 * eps * (12.0 * s11 / (9.0 * rc9) - 2.0 * s5 / rc3),
+                         pre * 4.0 * eps * (16.0 * s11 / rc9 - 12.0 * s5 / rc3));
+            }
+    }
+    means[0] = U;
+    means[1] = W;
+    s->forces_valid = false;
+    return MD_OK;
 }
 
 md_status md_profile(md_system *s, int32_t enable)

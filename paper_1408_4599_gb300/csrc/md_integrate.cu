@@ -1,8 +1,8 @@
 // md_integrate.cu -- leapfrog integrator (§3, Eqs. 2-3 translational,
 // Eqs. 4-5 rotational read as Fincham's quaternion leapfrog), fused with
 // the periodic wrap and the cell id + histogram of the next rebuild; the
-// kinetic-energy reduction at integer time steps; velocity rescaling (§2
-// NVT thermostat).  FP64 state and arithmetic.
+// kinetic-energy reduction at integer time steps (FP64); velocity
+// rescaling.  FP64 state; see k_integrate for the precision split.
 #include "md_internal.cuh"
 
 namespace {
@@ -43,45 +43,87 @@ __device__ __forceinline__ void normalise4(double q[4])
     q[3] *= inv;
 }
 
+// FP32 helpers for the rotational increments.
+__device__ __forceinline__ void omega_body_f(const float q[4], const float j[3], const float Iinv[3], float w[3])
+{
+    const float qw = q[0], qx = q[1], qy = q[2], qz = q[3];
+    const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
+    const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
+    const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
+    w[0] = Iinv[0] * (R00 * j[0] + R10 * j[1] + R20 * j[2]);
+    w[1] = Iinv[1] * (R01 * j[0] + R11 * j[1] + R21 * j[2]);
+    w[2] = Iinv[2] * (R02 * j[0] + R12 * j[1] + R22 * j[2]);
+}
+
+__device__ __forceinline__ void quat_rate_f(const float q[4], const float w[3], float qd[4])
+{
+    qd[0] = 0.5f * (-q[1] * w[0] - q[2] * w[1] - q[3] * w[2]);
+    qd[1] = 0.5f * (q[0] * w[0] + q[2] * w[2] - q[3] * w[1]);
+    qd[2] = 0.5f * (q[0] * w[1] + q[3] * w[0] - q[1] * w[2]);
+    qd[3] = 0.5f * (q[0] * w[2] + q[1] * w[1] - q[2] * w[0]);
+}
+
 // One leapfrog step per molecule (storage order), then wrap into [0, L),
 // cell id and histogram for the rebuild that follows.
+//
+// Precision split (GB300's FP64 pipe is a small fraction of its FP32 rate):
+// the state r, v, q, j and every update of it are FP64 (Eqs. 2-5 as
+// written); the rotational increment q_dot (from w = I^-1 A(q) j, the
+// half-step quaternion and its renormalisation) is formed in FP32 from the
+// rounded state, so its relative error (~1e-7) enters q only through the
+// dt-scaled update.  The final renormalisation of q uses the series
+// (1 + e)^(-1/2) = 1 - e/2 + 3e^2/8 - 5e^3/16 with e = |q|^2 - 1 (|e| ~ 1e-6),
+// exact to FP64 rounding.
 __global__ void k_integrate(Grid g, DevModel m, DevState d, double dt)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= d.n) return;
-    const double im = 1.0 / m.mass;
-    double r[3], v[3];
+    const double dtm = dt / m.mass;
     int cc[3];
     bool bad = false;
     for (int k = 0; k < 3; k++) {
-        v[k] = d.v[3 * s + k] + dt * d.F[3 * s + k] * im;  // Eq. 2
-        r[k] = d.r[3 * s + k] + dt * v[k];                  // Eq. 3
-        bad |= !isfinite(r[k]);
-        r[k] -= g.L[k] * floor(r[k] / g.L[k]);
-        if (r[k] >= g.L[k]) r[k] -= g.L[k];
-        if (r[k] < 0.0) r[k] = 0.0;
-        d.v[3 * s + k] = v[k];
-        d.r[3 * s + k] = r[k];
-        cc[k] = cell_axis(r[k], g.ell[k], g.nc[k]);
+        const double v = d.v[3 * s + k] + dtm * d.F[3 * s + k];  // Eq. 2
+        double r = d.r[3 * s + k] + dt * v;                        // Eq. 3
+        bad |= !isfinite(r);
+        if (r < 0.0) r += g.L[k];
+        else if (r >= g.L[k]) r -= g.L[k];
+        if (!(r >= 0.0 && r < g.L[k])) {  // moved more than a box length: general wrap
+            r -= g.L[k] * floor(r / g.L[k]);
+            if (r >= g.L[k]) r -= g.L[k];
+            if (r < 0.0) r = 0.0;
+        }
+        d.v[3 * s + k] = v;
+        d.r[3 * s + k] = r;
+        cc[k] = cell_axis(r, g.ell[k], g.nc[k]);
     }
     if (m.rot_dof > 0) {
         double q[4] = {d.q[4 * s], d.q[4 * s + 1], d.q[4 * s + 2], d.q[4 * s + 3]};
         double j[3] = {d.j[3 * s], d.j[3 * s + 1], d.j[3 * s + 2]};
         const double t[3] = {d.tau[3 * s], d.tau[3 * s + 1], d.tau[3 * s + 2]};
-        double jt[3], w[3], qd[4], qh[4];
-        for (int k = 0; k < 3; k++) jt[k] = j[k] + 0.5 * dt * t[k];  // j(t)
-        omega_body(q, jt, m.Iinv, w);
-        quat_rate(q, w, qd);
-        for (int k = 0; k < 4; k++) qh[k] = q[k] + 0.5 * dt * qd[k];  // q(t + dt/2)
-        normalise4(qh);
-        for (int k = 0; k < 3; k++) j[k] += dt * t[k];  // Eq. 4: j(t + dt/2)
-        omega_body(qh, j, m.Iinv, w);
-        quat_rate(qh, w, qd);
-        for (int k = 0; k < 4; k++) q[k] += dt * qd[k];  // Eq. 5: q(t + dt)
-        normalise4(q);
-        for (int k = 0; k < 4; k++) d.q[4 * s + k] = q[k];
+        const float Iinv[3] = {(float)m.Iinv[0], (float)m.Iinv[1], (float)m.Iinv[2]};
+        const float hdt = (float)(0.5 * dt);
+        float qf[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
+        float tf[3] = {(float)t[0], (float)t[1], (float)t[2]};
+        float jt[3], w[3], qd[4], qh[4];
+        for (int k = 0; k < 3; k++) jt[k] = (float)j[k] + hdt * tf[k];  // j(t)
+        omega_body_f(qf, jt, Iinv, w);
+        quat_rate_f(qf, w, qd);
+        for (int k = 0; k < 4; k++) qh[k] = qf[k] + hdt * qd[k];  // q(t + dt/2)
+        const float nh = rsqrtf(qh[0] * qh[0] + qh[1] * qh[1] + qh[2] * qh[2] + qh[3] * qh[3]);
+        for (int k = 0; k < 4; k++) qh[k] *= nh;
+        float jh[3];
+        for (int k = 0; k < 3; k++) {
+            j[k] += dt * t[k];  // Eq. 4: j(t + dt/2), FP64
+            jh[k] = (float)j[k];
+        }
+        omega_body_f(qh, jh, Iinv, w);
+        quat_rate_f(qh, w, qd);
+        for (int k = 0; k < 4; k++) q[k] += dt * (double)qd[k];  // Eq. 5: q(t + dt)
+        const double e = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3] - 1.0;
+        const double inv = 1.0 + e * (-0.5 + e * (0.375 - 0.3125 * e));
+        for (int k = 0; k < 4; k++) d.q[4 * s + k] = q[k] * inv;
         for (int k = 0; k < 3; k++) d.j[3 * s + k] = j[k];
-        bad |= !isfinite(q[0]);
+        bad |= !isfinite(q[0]) || fabs(e) > 0.01;
     }
     if (bad) atomicExch(&d.flags[FLAG_NONFINITE], 1);
     const int c = (cc[2] * g.nc[1] + cc[1]) * g.nc[0] + cc[0];

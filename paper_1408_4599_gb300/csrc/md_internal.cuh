@@ -9,7 +9,6 @@
 #define MD_MAX_SITES 8
 #define MD_MAX_TYPES 8
 #define MD_WARPS 4          // warps per force block (one cell per warp)
-#define MD_HIT_CAP 32       // per-lane hit-list capacity before a flush
 
 // Roles a merged interaction site can carry (§2).  A site has one position
 // and at most one axis, shared by its dipole and quadrupole roles.
@@ -30,6 +29,9 @@ struct DevModel {
     float eps24[MD_MAX_TYPES][MD_MAX_TYPES];  // 24 eps_ab
     float sig2[MD_MAX_TYPES][MD_MAX_TYPES];   // sigma_ab^2
     float ushift[MD_MAX_TYPES][MD_MAX_TYPES]; // LJTS shift u_ab(rc) (0 if unshifted)
+    float isig[MD_MAX_TYPES][MD_MAX_TYPES];     // 1 / sigma_ab
+    float ushift_e[MD_MAX_TYPES][MD_MAX_TYPES]; // shift / eps_ab
+    float dshift_s[MD_MAX_TYPES][MD_MAX_TYPES]; // d(shift / eps_ab) / d sigma_ab
     float frf;                      // reaction-field factor / rc^3
     int site_pairs_per_mol_pair;    // n_lj^2 + n_el^2 of the user's entities
     int single_lj_at_com;           // 1: one LJ site at the centre of mass, nothing else
@@ -70,6 +72,7 @@ struct DevState {
     double *partials;               // force-kernel block partials, 8 per block
     double *kin_partials;           // kinetic partials, 4 per block
     int *flags;                     // [0] non-finite, [1] overflow, [2] timeout
+    float *facc;                    // 6 x n FP32 force/torque accumulators (half shell)
 };
 
 // Partial-sum layout of the force kernel (per block).
@@ -90,4 +93,7 @@ cudaError_t launch_scatter_out(const DevState &d, const double *src, int width, 
 cudaError_t launch_gather_in(DevState &d, const double *src, int width, double *dst, cudaStream_t s);
 cudaError_t launch_prepare_input(const Grid &g, DevState &d, cudaStream_t s);
 int force_blocks_default();
+int adjoint_nacc(const DevModel &m);
+cudaError_t launch_adjoint(const Grid &g, const DevModel &m, const DevState &d, int half_shell, int n_blocks,
+                           double *partials, int nacc, cudaStream_t s);
 int scan_blocks(long long ncell);

@@ -1,0 +1,538 @@
+// md_pair.cuh -- site-site interaction laws (§2: LJ Eq. 1 with Lorentz-
+// Berthelot mixing, point charges, dipoles, linear quadrupoles; §3 reaction
+// field) and the linked-cell traversal (§3: 27-cell stencil, or the 14-cell
+// Newton-3 half stencil) shared by the force, adjoint and batched kernels.
+//
+// Traversal (one warp per i-cell):
+//   * the stencil's candidate molecules are staged in shared memory with the
+//     periodic image offset already applied (FP32, i-cell frame);
+//   * for each i molecule all 32 lanes test 32 candidates at a time
+//     (FP32 centre-of-mass distance; a test within a narrow band of r_c^2 is
+//     redone in FP64 from the FP64 state, so the pair set is the FP64
+//     definition's);
+//   * hits are ballot-compacted into a per-warp queue and handed to the
+//     pair operation 32 at a time, so the expensive site-site math runs on
+//     packed lanes (only ~16% of examined pairs interact, §3).
+//   * A chunk holds pairs of one i molecule, so its j's are distinct.
+#pragma once
+
+#include "md_internal.cuh"
+
+namespace mdk {
+
+constexpr int EL_ROLES = ROLE_CHG | ROLE_DIP | ROLE_QUAD;
+constexpr int AX_ROLES = ROLE_DIP | ROLE_QUAD;
+constexpr unsigned FULLMASK = 0xffffffffu;
+
+__host__ __device__ constexpr int sig_role(unsigned R, int a) { return (int)((R >> (4 * a)) & 15u); }
+__host__ __device__ constexpr int sig_slot(unsigned R, int a)
+{
+    int k = 0;
+    for (int b = 0; b < a; b++) k += (sig_role(R, b) & AX_ROLES) ? 1 : 0;
+    return (sig_role(R, a) & AX_ROLES) ? k : -1;
+}
+__host__ __device__ constexpr int sig_na(unsigned R, int S)
+{
+    int k = 0;
+    for (int b = 0; b < S; b++) k += (sig_role(R, b) & AX_ROLES) ? 1 : 0;
+    return k;
+}
+__host__ __device__ constexpr unsigned sigkey(int r0, int r1 = 0, int r2 = 0, int r3 = 0, int r4 = 0, int r5 = 0,
+                                              int r6 = 0, int r7 = 0)
+{
+    return (unsigned)r0 | ((unsigned)r1 << 4) | ((unsigned)r2 << 8) | ((unsigned)r3 << 12) | ((unsigned)r4 << 16) |
+           ((unsigned)r5 << 20) | ((unsigned)r6 << 24) | ((unsigned)r7 << 28);
+}
+
+// Signatures compiled ahead of time; any other model runs SigDyn.
+constexpr unsigned SIG_2CLJ = sigkey(ROLE_LJ, ROLE_LJ);
+constexpr unsigned SIG_2CLJQ = sigkey(ROLE_LJ, ROLE_LJ, ROLE_QUAD);
+constexpr unsigned SIG_2CLJDQ = sigkey(ROLE_LJ, ROLE_LJ, ROLE_DIP | ROLE_QUAD);
+constexpr unsigned SIG_4SITE = sigkey(ROLE_LJ, ROLE_LJ | ROLE_CHG, ROLE_LJ | ROLE_CHG, ROLE_DIP, ROLE_QUAD);
+
+// Compile-time site-role signature: S sites, 4 role bits per site.
+template <int S_, unsigned R_, bool SINGLE_ = false>
+struct SigStatic {
+    static constexpr int S = S_;
+    static constexpr bool DYN = false;
+    static constexpr bool SINGLE = SINGLE_;
+    static constexpr int K = S_ + sig_na(R_, S_);
+    __device__ __forceinline__ static constexpr int role(int a, const DevModel &) { return sig_role(R_, a); }
+    __device__ __forceinline__ static constexpr int slot(int a, const DevModel &) { return sig_slot(R_, a); }
+    __device__ __forceinline__ static int kk(const DevModel &) { return K; }
+    __device__ __forceinline__ static int s_of(const DevModel &) { return S_; }
+};
+
+// Run-time signature for any other model (up to MD_MAX_SITES sites).
+struct SigDyn {
+    static constexpr int S = MD_MAX_SITES;
+    static constexpr bool DYN = true;
+    static constexpr bool SINGLE = false;
+    __device__ __forceinline__ static int role(int a, const DevModel &m) { return a < m.S ? m.roles[a] : 0; }
+    __device__ __forceinline__ static int slot(int a, const DevModel &m) { return m.axis_slot[a]; }
+    __device__ __forceinline__ static int kk(const DevModel &m) { return m.S + m.NA; }
+    __device__ __forceinline__ static int s_of(const DevModel &m) { return m.S; }
+};
+
+// Dispatch of a model to its compiled signature: f.template operator()<SIG>().
+template <class F>
+__host__ auto dispatch_sig(const DevModel &m, F &&f)
+{
+    unsigned key = 0;
+    for (int a = 0; a < m.S; a++) key |= (unsigned)m.roles[a] << (4 * a);
+    if (m.single_lj_at_com) return f.template operator()<SigStatic<1, ROLE_LJ, true>>();
+    if (m.S == 2 && key == SIG_2CLJ) return f.template operator()<SigStatic<2, SIG_2CLJ>>();
+    if (m.S == 3 && key == SIG_2CLJQ) return f.template operator()<SigStatic<3, SIG_2CLJQ>>();
+    if (m.S == 3 && key == SIG_2CLJDQ) return f.template operator()<SigStatic<3, SIG_2CLJDQ>>();
+    if (m.S == 5 && key == SIG_4SITE) return f.template operator()<SigStatic<5, SIG_4SITE>>();
+    return f.template operator()<SigDyn>();
+}
+
+// Half-shell stencil: the cell itself and the 13 neighbours that follow it
+// in (z, y, x) lexicographic order.
+__device__ __forceinline__ void stencil_offset(bool half, int o, int &dx, int &dy, int &dz)
+{
+    if (half) {
+        const int h = o == 0 ? 13 : o + 13;  // the 13 forward offsets are full-stencil indices 14..26
+        dx = h % 3 - 1;
+        dy = (h / 3) % 3 - 1;
+        dz = h / 9 - 1;
+    } else {
+        dx = o % 3 - 1;
+        dy = (o / 3) % 3 - 1;
+        dz = o / 9 - 1;
+    }
+}
+
+__device__ __forceinline__ int wrap_axis(int c, int d, int nc, int &k)
+{
+    int x = c + d;
+    k = 0;
+    if (x < 0) {
+        x += nc;
+        k = -1;
+    } else if (x >= nc) {
+        x -= nc;
+        k = 1;
+    }
+    return x;
+}
+
+// One electrostatic role pair's unit-strength energy and its partials with
+// respect to r (as n U: U is homogeneous of degree -n in r), pa = e_a.xh,
+// pb = e_b.xh and cab = e_a.e_b (x = r_a - r_b, xh = x/r, k_C = 1):
+//   q q: 1/r;  q mu: pb/r^2;  mu q: -pa/r^2;  mu mu: (cab - 3 pa pb)/r^3;
+//   q Q: (3 pb^2 - 1)/(2 r^3);  Q q: (3 pa^2 - 1)/(2 r^3);
+//   mu Q: 3/(2 r^4) [-pa (5 pb^2 - 1) + 2 pb cab];
+//   Q mu: 3/(2 r^4) [pb (5 pa^2 - 1) - 2 pa cab];
+//   Q Q: 3/(4 r^5) [1 - 5 pa^2 - 5 pb^2 - 15 pa^2 pb^2 + 2 (cab - 5 pa pb)^2];
+//   reaction field (dipole pairs, §3): -f_RF cab / rc^3 (no r dependence).
+struct Law {
+    float U, nU, Upa, Upb, Ucab;
+};
+
+enum { LAW_QQ, LAW_QMU, LAW_MUQ, LAW_MUMU, LAW_QQUAD, LAW_QUADQ, LAW_MUQUAD, LAW_QUADMU, LAW_QUADQUAD };
+
+template <int L>
+__device__ __forceinline__ Law law(float ir, float pa, float pb, float cab, float frf)
+{
+    Law o{0.f, 0.f, 0.f, 0.f, 0.f};
+    const float u2 = ir * ir, u3 = u2 * ir;
+    if (L == LAW_QQ) {
+        o.U = ir;
+        o.nU = ir;
+    } else if (L == LAW_QMU) {
+        o.U = pb * u2;
+        o.nU = 2.f * o.U;
+        o.Upb = u2;
+    } else if (L == LAW_MUQ) {
+        o.U = -pa * u2;
+        o.nU = 2.f * o.U;
+        o.Upa = -u2;
+    } else if (L == LAW_MUMU) {
+        const float t = (cab - 3.f * pa * pb) * u3;
+        o.U = t - frf * cab;
+        o.nU = 3.f * t;
+        o.Upa = -3.f * pb * u3;
+        o.Upb = -3.f * pa * u3;
+        o.Ucab = u3 - frf;
+    } else if (L == LAW_QQUAD) {
+        o.U = 0.5f * (3.f * pb * pb - 1.f) * u3;
+        o.nU = 3.f * o.U;
+        o.Upb = 3.f * pb * u3;
+    } else if (L == LAW_QUADQ) {
+        o.U = 0.5f * (3.f * pa * pa - 1.f) * u3;
+        o.nU = 3.f * o.U;
+        o.Upa = 3.f * pa * u3;
+    } else if (L == LAW_MUQUAD) {
+        const float c = 1.5f * u2 * u2;
+        o.U = c * (2.f * pb * cab - pa * (5.f * pb * pb - 1.f));
+        o.nU = 4.f * o.U;
+        o.Upa = c * (1.f - 5.f * pb * pb);
+        o.Upb = c * (2.f * cab - 10.f * pa * pb);
+        o.Ucab = 2.f * c * pb;
+    } else if (L == LAW_QUADMU) {
+        const float c = 1.5f * u2 * u2;
+        o.U = c * (pb * (5.f * pa * pa - 1.f) - 2.f * pa * cab);
+        o.nU = 4.f * o.U;
+        o.Upb = c * (5.f * pa * pa - 1.f);
+        o.Upa = c * (10.f * pa * pb - 2.f * cab);
+        o.Ucab = -2.f * c * pa;
+    } else {
+        const float c = 0.75f * u2 * u3;
+        const float pa2 = pa * pa, pb2 = pb * pb;
+        const float tt = cab - 5.f * pa * pb;
+        o.U = c * (1.f - 5.f * (pa2 + pb2) - 15.f * pa2 * pb2 + 2.f * tt * tt);
+        o.nU = 5.f * o.U;
+        o.Upa = -c * (10.f * pa + 30.f * pa * pb2 + 20.f * pb * tt);
+        o.Upb = -c * (10.f * pb + 30.f * pa2 * pb + 20.f * pa * tt);
+        o.Ucab = 4.f * c * tt;
+    }
+    return o;
+}
+
+__device__ __forceinline__ void law_acc(Law &t, const Law &l, float s)
+{
+    t.U += s * l.U;
+    t.nU += s * l.nU;
+    t.Upa += s * l.Upa;
+    t.Upb += s * l.Upb;
+    t.Ucab += s * l.Ucab;
+}
+
+// Electrostatic interaction of site a (on i) with site b (on j) with the
+// strengths applied: energy, force on a, orientation torques e x (-dU/de).
+template <bool JSIDE>
+__device__ __forceinline__ void elec_site(const int ra, const int rb, const float qa, const float mua, const float Qa,
+                                          const float qb, const float mub, const float Qb, const float frf,
+                                          const float x, const float y, const float z, const float ir,
+                                          const float4 &ea, const float4 &eb, float &U, float &fx, float &fy,
+                                          float &fz, float (&ti)[3], float (&tj)[3])
+{
+    const float xh = x * ir, yh = y * ir, zh = z * ir;
+    const bool axa = (ra & AX_ROLES) != 0, axb = (rb & AX_ROLES) != 0;
+    const float pa = axa ? (ea.x * xh + ea.y * yh + ea.z * zh) : 0.f;
+    const float pb = axb ? (eb.x * xh + eb.y * yh + eb.z * zh) : 0.f;
+    const float cab = (axa && axb) ? (ea.x * eb.x + ea.y * eb.y + ea.z * eb.z) : 0.f;
+    Law t{0.f, 0.f, 0.f, 0.f, 0.f};
+    if ((ra & ROLE_CHG) && (rb & ROLE_CHG)) law_acc(t, law<LAW_QQ>(ir, pa, pb, cab, 0.f), qa * qb);
+    if ((ra & ROLE_CHG) && (rb & ROLE_DIP)) law_acc(t, law<LAW_QMU>(ir, pa, pb, cab, 0.f), qa * mub);
+    if ((ra & ROLE_DIP) && (rb & ROLE_CHG)) law_acc(t, law<LAW_MUQ>(ir, pa, pb, cab, 0.f), mua * qb);
+    if ((ra & ROLE_DIP) && (rb & ROLE_DIP)) law_acc(t, law<LAW_MUMU>(ir, pa, pb, cab, frf), mua * mub);
+    if ((ra & ROLE_CHG) && (rb & ROLE_QUAD)) law_acc(t, law<LAW_QQUAD>(ir, pa, pb, cab, 0.f), qa * Qb);
+    if ((ra & ROLE_QUAD) && (rb & ROLE_CHG)) law_acc(t, law<LAW_QUADQ>(ir, pa, pb, cab, 0.f), Qa * qb);
+    if ((ra & ROLE_DIP) && (rb & ROLE_QUAD)) law_acc(t, law<LAW_MUQUAD>(ir, pa, pb, cab, 0.f), mua * Qb);
+    if ((ra & ROLE_QUAD) && (rb & ROLE_DIP)) law_acc(t, law<LAW_QUADMU>(ir, pa, pb, cab, 0.f), Qa * mub);
+    if ((ra & ROLE_QUAD) && (rb & ROLE_QUAD)) law_acc(t, law<LAW_QUADQUAD>(ir, pa, pb, cab, 0.f), Qa * Qb);
+    U += t.U;
+    // dU/dx = xh (Ur - (Upa pa + Upb pb)/r) + (Upa e_a + Upb e_b)/r, Ur = -nU/r
+    const float cx = -(t.nU + t.Upa * pa + t.Upb * pb) * ir;
+    const float ua = t.Upa * ir, ub = t.Upb * ir;
+    fx -= cx * xh + ua * ea.x + ub * eb.x;
+    fy -= cx * yh + ua * ea.y + ub * eb.y;
+    fz -= cx * zh + ua * ea.z + ub * eb.z;
+    float cex = 0.f, cey = 0.f, cez = 0.f;
+    if (axa && axb) {
+        cex = ea.y * eb.z - ea.z * eb.y;
+        cey = ea.z * eb.x - ea.x * eb.z;
+        cez = ea.x * eb.y - ea.y * eb.x;
+    }
+    if (axa) {  // e_a x (-(Upa xh + Ucab e_b))
+        ti[0] -= t.Upa * (ea.y * zh - ea.z * yh) + t.Ucab * cex;
+        ti[1] -= t.Upa * (ea.z * xh - ea.x * zh) + t.Ucab * cey;
+        ti[2] -= t.Upa * (ea.x * yh - ea.y * xh) + t.Ucab * cez;
+    }
+    if (JSIDE && axb) {  // e_b x (-(Upb xh + Ucab e_a))
+        tj[0] += -t.Upb * (eb.y * zh - eb.z * yh) + t.Ucab * cex;
+        tj[1] += -t.Upb * (eb.z * xh - eb.x * zh) + t.Ucab * cey;
+        tj[2] += -t.Upb * (eb.x * yh - eb.y * xh) + t.Ucab * cez;
+    }
+}
+
+// The i molecule of the current traversal step, in registers.
+template <class SIG>
+struct IMol {
+    float4 c;                 // centre of mass (cell-centre frame)
+    float d[SIG::S][3];       // space-frame site offsets
+    float4 e[SIG::S];         // space-frame axes
+    int slot;
+};
+
+template <class SIG>
+__device__ __forceinline__ void load_i(const DevModel &m, const float4 *com, const float4 *geo, int K, int si,
+                                       IMol<SIG> &I)
+{
+    I.slot = si;
+    I.c = com[si];
+#pragma unroll
+    for (int a = 0; a < SIG::S; a++) {
+        I.d[a][0] = I.d[a][1] = I.d[a][2] = 0.f;
+        I.e[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!SIG::SINGLE && SIG::role(a, m)) {
+            const float4 t4 = geo[(long long)si * K + a];
+            I.d[a][0] = t4.x;
+            I.d[a][1] = t4.y;
+            I.d[a][2] = t4.z;
+            if (SIG::role(a, m) & AX_ROLES) I.e[a] = geo[(long long)si * K + SIG::s_of(m) + SIG::slot(a, m)];
+        }
+    }
+}
+
+// Pair of molecules: force on i, torque on i (lever arms + orientation),
+// torque on j (JSIDE), energy.  Site forces are summed per site of i inside
+// the pair so that the lever-arm torque costs 6 FMA per site of i.
+template <class SIG, bool JSIDE>
+__device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, const float X1, const float X2,
+                                         const IMol<SIG> &I, const float4 *__restrict__ gj, float (&Fo)[3],
+                                         float (&to)[3], float (&tj)[3], float &Uo)
+{
+    constexpr int S = SIG::S;
+    float fa[S][3];
+#pragma unroll
+    for (int a = 0; a < S; a++) fa[a][0] = fa[a][1] = fa[a][2] = 0.f;
+    float ti[3] = {0.f, 0.f, 0.f};
+    float U = 0.f;
+    tj[0] = tj[1] = tj[2] = 0.f;
+    if (SIG::SINGLE) {
+        const float r2 = X0 * X0 + X1 * X1 + X2 * X2;
+        const float ir2 = __fdividef(1.f, r2);
+        const float s2 = m.sig2[0][0] * ir2;
+        const float s6 = s2 * s2 * s2;
+        const float fr = m.eps24[0][0] * s6 * (2.f * s6 - 1.f) * ir2;
+        U = m.eps4[0][0] * s6 * (s6 - 1.f) - m.ushift[0][0];
+        fa[0][0] = fr * X0;
+        fa[0][1] = fr * X1;
+        fa[0][2] = fr * X2;
+    } else {
+#pragma unroll
+        for (int b = 0; b < S; b++) {
+            const int rb = SIG::role(b, m);
+            if (rb == 0) continue;
+            const float4 db = __ldg(gj + b);
+            float4 eb = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rb & AX_ROLES) eb = __ldg(gj + SIG::s_of(m) + SIG::slot(b, m));
+            float fbx = 0.f, fby = 0.f, fbz = 0.f;
+#pragma unroll
+            for (int a = 0; a < S; a++) {
+                const int ra = SIG::role(a, m);
+                const bool lj = (ra & ROLE_LJ) && (rb & ROLE_LJ);
+                const bool el = (ra & EL_ROLES) && (rb & EL_ROLES);
+                if (!lj && !el) continue;
+                const float x = X0 + I.d[a][0] - db.x;
+                const float y = X1 + I.d[a][1] - db.y;
+                const float z = X2 + I.d[a][2] - db.z;
+                const float r2 = x * x + y * y + z * z;
+                float fx = 0.f, fy = 0.f, fz = 0.f;
+                float ir = 0.f, ir2;
+                if (el) {
+                    ir = rsqrtf(r2);
+                    ir2 = ir * ir;
+                } else {
+                    ir2 = __fdividef(1.f, r2);
+                }
+                if (lj) {
+                    const int ta = m.lj_type[a], tb = m.lj_type[b];
+                    const float s2 = m.sig2[ta][tb] * ir2;
+                    const float s6 = s2 * s2 * s2;
+                    const float fr = m.eps24[ta][tb] * s6 * (2.f * s6 - 1.f) * ir2;
+                    U += m.eps4[ta][tb] * s6 * (s6 - 1.f) - m.ushift[ta][tb];
+                    fx = fr * x;
+                    fy = fr * y;
+                    fz = fr * z;
+                }
+                if (el) {
+                    elec_site<JSIDE>(ra, rb, m.chg[a], m.mu[a], m.Q[a], m.chg[b], m.mu[b], m.Q[b], m.frf, x, y, z,
+                                     ir, I.e[a], eb, U, fx, fy, fz, ti, tj);
+                }
+                fa[a][0] += fx;
+                fa[a][1] += fy;
+                fa[a][2] += fz;
+                fbx += fx;
+                fby += fy;
+                fbz += fz;
+            }
+            if (JSIDE) {
+                tj[0] -= db.y * fbz - db.z * fby;
+                tj[1] -= db.z * fbx - db.x * fbz;
+                tj[2] -= db.x * fby - db.y * fbx;
+            }
+        }
+    }
+    float F0 = 0.f, F1 = 0.f, F2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < S; a++) {
+        F0 += fa[a][0];
+        F1 += fa[a][1];
+        F2 += fa[a][2];
+        if (!SIG::SINGLE) {
+            ti[0] += I.d[a][1] * fa[a][2] - I.d[a][2] * fa[a][1];
+            ti[1] += I.d[a][2] * fa[a][0] - I.d[a][0] * fa[a][2];
+            ti[2] += I.d[a][0] * fa[a][1] - I.d[a][1] * fa[a][0];
+        }
+    }
+    Fo[0] = F0;
+    Fo[1] = F1;
+    Fo[2] = F2;
+    to[0] = ti[0];
+    to[1] = ti[1];
+    to[2] = ti[2];
+    Uo = U;
+}
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
+{
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// ------------------------------------------------------------- traversal
+constexpr int JCAP = 256;   // staged candidates per segment
+constexpr int QCAP = 64;    // hit queue
+
+// Per-warp staging area; Extra is the pair operation's own shared state.
+template <class Extra>
+struct WarpTile {
+    float4 jc[JCAP];          // candidate COM + image offset (i-cell frame); w = storage slot bits
+    unsigned char jst[JCAP];  // stencil index of the candidate's cell
+    int queue[QCAP];
+    Extra x;
+};
+
+// The periodic grid a cell belongs to (one system, or one replica of a batch).
+struct GridView {
+    int nc[3];
+    float ellf[3];
+    double L[3];
+    double rc2;
+    float rc2f, bandf;
+    long long cell0;          // first global cell index of this grid
+};
+
+// Visits every interacting pair (i in cell c, j in the stencil) in chunks
+// of <= 32 pairs of one i.  Op provides:
+//   seg_begin(T, nj, lane)            after a segment has been staged
+//   seg_end(T, nj, lane)              after all i's of a pass met the segment
+//   i_begin(I, il)                    before the candidates of one i
+//   pair(T, I, k, X0, X1, X2, lane)   for the lane's queued pair (lane < nq)
+//   i_end(I, il, lane)                after the candidates of one i
+//   pass_begin(ig, ni, lane) / pass_end(s0, ig, ni, lane)
+//   count_examined(n)
+// cell_start holds global slots; c is the cell index inside the grid.
+template <class SIG, bool HALF, class Op, class Extra>
+__device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView &g, const int *__restrict__ cell_start,
+                                              const float4 *__restrict__ com, const float4 *__restrict__ geo,
+                                              const double *__restrict__ r64, int K, long long c, WarpTile<Extra> &T,
+                                              Op &op, int lane)
+{
+    constexpr int IMAX = Op::IMAX;
+    const int s0 = cell_start[g.cell0 + c];
+    const int n_i = cell_start[g.cell0 + c + 1] - s0;
+    if (n_i == 0) return;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int NOFF = HALF ? 14 : 27;
+    const int cx = (int)(c % g.nc[0]);
+    const int cy = (int)((c / g.nc[0]) % g.nc[1]);
+    const int cz = (int)(c / ((long long)g.nc[0] * g.nc[1]));
+    for (int ig = 0; ig < n_i; ig += IMAX) {
+        const int ni = min(IMAX, n_i - ig);
+        op.pass_begin(ig, ni, lane);
+        int o_cur = 0, o_pos = 0;
+        while (o_cur < NOFF) {
+            int nj = 0, self_lo = 0, self_n = 0, self_base = 0;
+            while (o_cur < NOFF && nj < JCAP) {
+                int dx, dy, dz, kx, ky, kz;
+                stencil_offset(HALF, o_cur, dx, dy, dz);
+                const int nx = wrap_axis(cx, dx, g.nc[0], kx);
+                const int ny = wrap_axis(cy, dy, g.nc[1], ky);
+                const int nz = wrap_axis(cz, dz, g.nc[2], kz);
+                const long long cn = g.cell0 + ((long long)nz * g.nc[1] + ny) * g.nc[0] + nx;
+                const int j0 = cell_start[cn], cnt = cell_start[cn + 1] - j0;
+                const int take = min(cnt - o_pos, JCAP - nj);
+                if (dx == 0 && dy == 0 && dz == 0) {  // the i-cell: local index self_lo + (k - self_base)
+                    self_lo = o_pos;
+                    self_n = take;
+                    self_base = nj;  // 0 in the half shell (stencil index 0 opens a segment)
+                }
+                const float ox = dx * g.ellf[0], oy = dy * g.ellf[1], oz = dz * g.ellf[2];
+                for (int t = lane; t < take; t += 32) {
+                    const int js = j0 + o_pos + t;
+                    const float4 cj = com[js];
+                    T.jc[nj + t] = make_float4(cj.x + ox, cj.y + oy, cj.z + oz, __int_as_float(js));
+                    T.jst[nj + t] = (unsigned char)o_cur;
+                }
+                nj += take;
+                o_pos += take;
+                if (o_pos >= cnt) {
+                    o_cur++;
+                    o_pos = 0;
+                }
+            }
+            op.seg_begin(T, nj, lane);
+            __syncwarp();
+            for (int il = ig; il < ig + ni; il++) {
+                IMol<SIG> I;
+                load_i<SIG>(m, com, geo, K, s0 + il, I);
+                op.i_begin(I, il);
+                const int skip_to = (self_n > 0 && HALF) ? max(0, min(self_n, il - self_lo + 1)) : 0;
+                const int self_k =
+                    (self_n > 0 && !HALF && il >= self_lo && il < self_lo + self_n) ? self_base + (il - self_lo) : -1;
+                int qn = 0, nexam = 0;
+                for (int kb = skip_to; kb < nj; kb += 32) {
+                    const int k = kb + lane;
+                    bool hit = false;
+                    if (k < nj && k != self_k) {
+                        nexam++;
+                        const float4 cj = T.jc[k];
+                        const float X0 = I.c.x - cj.x, X1 = I.c.y - cj.y, X2 = I.c.z - cj.z;
+                        const float d2 = X0 * X0 + X1 * X1 + X2 * X2;
+                        hit = d2 < g.rc2f;
+                        if (fabsf(d2 - g.rc2f) < g.bandf) {
+                            int dx, dy, dz, kx, ky, kz;
+                            stencil_offset(HALF, T.jst[k], dx, dy, dz);
+                            wrap_axis(cx, dx, g.nc[0], kx);
+                            wrap_axis(cy, dy, g.nc[1], ky);
+                            wrap_axis(cz, dz, g.nc[2], kz);
+                            const double *ri = r64 + 3LL * I.slot, *rj = r64 + 3LL * __float_as_int(cj.w);
+                            const double e0 = __dsub_rn(__dsub_rn(ri[0], rj[0]), (double)kx * g.L[0]);
+                            const double e1 = __dsub_rn(__dsub_rn(ri[1], rj[1]), (double)ky * g.L[1]);
+                            const double e2 = __dsub_rn(__dsub_rn(ri[2], rj[2]), (double)kz * g.L[2]);
+                            hit = __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2)) < g.rc2;
+                        }
+                    }
+                    const unsigned bal = __ballot_sync(FULLMASK, hit);
+                    if (hit) T.queue[qn + __popc(bal & lt_mask)] = k;
+                    qn += __popc(bal);
+                    if (qn >= 32) {
+                        __syncwarp();
+                        const int kq = T.queue[lane];
+                        const float4 cj = T.jc[kq];
+                        op.pair(T, I, kq, I.c.x - cj.x, I.c.y - cj.y, I.c.z - cj.z, __float_as_int(cj.w), lane);
+                        __syncwarp();
+                        if (lane < qn - 32) T.queue[lane] = T.queue[32 + lane];
+                        qn -= 32;
+                    }
+                }
+                if (qn > 0) {
+                    __syncwarp();
+                    if (lane < qn) {
+                        const int kq = T.queue[lane];
+                        const float4 cj = T.jc[kq];
+                        op.pair(T, I, kq, I.c.x - cj.x, I.c.y - cj.y, I.c.z - cj.z, __float_as_int(cj.w), lane);
+                    }
+                    __syncwarp();
+                }
+                op.count_examined(nexam);
+                op.i_end(I, il, lane);
+            }
+            __syncwarp();
+            op.seg_end(T, nj, lane);
+            __syncwarp();
+        }
+        op.pass_end(s0, ig, ni, lane);
+        __syncwarp();
+    }
+}
+
+}  // namespace mdk

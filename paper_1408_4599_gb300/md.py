@@ -66,7 +66,8 @@ _lib = None
 # Every symbol include/md.h declares (checked by the CPU test suite).
 EXPORTS = ("md_create", "md_set_molecules", "md_compute_forces", "md_step", "md_energy_virial",
            "md_get_molecules", "md_get_forces", "md_n_molecules", "md_sync", "md_profile", "md_kernel_times_get",
-           "md_destroy", "md_status_str", "md_last_error")
+           "md_destroy", "md_status_str", "md_last_error", "md_n_params", "md_get_params", "md_set_params",
+           "md_param_grad")
 
 
 def lib():
@@ -90,6 +91,11 @@ def lib():
         L.md_sync.argtypes = [vp, vp]
         L.md_profile.argtypes = [vp, i32]
         L.md_kernel_times_get.argtypes = [vp, C.POINTER(md_kernel_times)]
+        L.md_n_params.argtypes = [vp]
+        L.md_n_params.restype = i32
+        L.md_get_params.argtypes = [vp, dp]
+        L.md_set_params.argtypes = [vp, dp, i32]
+        L.md_param_grad.argtypes = [vp, i32, i64, vp, vp, i32, dp, dp, dp, vp]
         L.md_kinetic_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, C.c_double, dp, C.c_double, vp, vp]
         L.md_kinetic_noalloc.restype = C.c_int
         L.md_destroy.argtypes = [vp]
@@ -99,7 +105,8 @@ def lib():
         L.md_last_error.argtypes = [vp]
         L.md_last_error.restype = C.c_char_p
         for name in ("md_create", "md_set_molecules", "md_compute_forces", "md_step", "md_energy_virial",
-                     "md_get_molecules", "md_get_forces", "md_sync", "md_profile", "md_kernel_times_get"):
+                     "md_get_molecules", "md_get_forces", "md_sync", "md_profile", "md_kernel_times_get",
+                     "md_get_params", "md_set_params", "md_param_grad"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -273,6 +280,36 @@ def md_kernel_times_get(h) -> dict:
     return t.as_dict()
 
 
+def md_n_params(h) -> int:
+    return int(lib().md_n_params(h))
+
+
+def md_get_params(h) -> np.ndarray:
+    th = np.zeros(md_n_params(h))
+    _check(lib().md_get_params(h, th.ctypes.data_as(dp)), h)
+    return th
+
+
+def md_set_params(h, theta):
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    _check(lib().md_set_params(h, th.ctypes.data_as(dp), int(th.shape[0])), h)
+
+
+def md_param_grad(h, r_all, q_all, stream=None):
+    """(dU/dtheta, dW/dtheta, <U>, <W>) over the configurations r_all
+    (n_cfg x n x 3) and q_all (n_cfg x n x 4), host arrays or device tensors."""
+    rp, dev, rk = _ptr(r_all)
+    qp, dq, qk = _ptr(q_all)
+    if dev != dq:
+        raise ValueError("r_all and q_all must live on the same side")
+    n_cfg, n = int(rk.shape[0]), int(rk.shape[1])
+    P = md_n_params(h)
+    dU, dW, means = np.zeros(P), np.zeros(P), np.zeros(2)
+    _check(lib().md_param_grad(h, n_cfg, n, rp, qp, dev, dU.ctypes.data_as(dp), dW.ctypes.data_as(dp),
+                               means.ctypes.data_as(dp), _stream_ptr(stream)), h)
+    return dU, dW, float(means[0]), float(means[1])
+
+
 def md_kinetic_noalloc(v, q, j, F, tau, mass, moments, dt, K_out, stream=None):
     """K_out (device float64 tensor of 2) <- (K_trans, K_rot); allocates nothing."""
     ptrs = [_ptr(a) for a in (v, q, j, F, tau, K_out)]
@@ -315,6 +352,15 @@ class System:
 
     def forces(self, **kw):
         return md_get_forces(self.h, **kw)
+
+    def params(self):
+        return md_get_params(self.h)
+
+    def set_params(self, theta):
+        md_set_params(self.h, theta)
+
+    def param_grad(self, r_all, q_all, stream=None):
+        return md_param_grad(self.h, r_all, q_all, stream)
 
     def close(self):
         if self.h:
