@@ -57,8 +57,8 @@ __host__ __device__ constexpr int sig_lj(unsigned R, int a)
 template <class SIG>
 struct AdjLayout;
 
-template <int S_, unsigned R_, bool SG_>
-struct AdjLayout<SigStatic<S_, R_, SG_>> {
+template <int S_, unsigned R_, bool SG_, unsigned TY_>
+struct AdjLayout<SigStatic<S_, R_, SG_, TY_>> {
     static constexpr int NLJ = sig_nlj(R_, S_);
     static constexpr int NE = sig_ne(R_, S_);
     static constexpr int NACC = 4 * NLJ * NLJ + 2 * NE * NE + 2;  // + U, W
@@ -144,7 +144,7 @@ struct AdjOp {
                 const float r2 = x * x + y * y + z * z;
                 const float Xx = X0 * x + X1 * y + X2 * z;
                 if (lj) {
-                    const int ta = m.lj_type[a], tb = m.lj_type[b];
+                    const int ta = SIG::type(a, m), tb = SIG::type(b, m);
                     const float ir2 = __fdividef(1.f, r2);
                     const float s2 = m.sig2[ta][tb] * ir2;
                     const float s6 = s2 * s2 * s2, s12 = s6 * s6;

@@ -589,7 +589,7 @@ md_status md_create(const double box[3], double cutoff, const md_site_types *typ
     s->d.K = s->m.single_lj_at_com ? 0 : s->m.S + s->m.NA;
 
     long long fb = (ncell + MD_WARPS - 1) / MD_WARPS;
-    s->n_force_blocks = (int)(fb < 152 * 4 ? fb : 152 * 4);  // persistent: grid-stride over cells
+    s->n_force_blocks = (int)(fb < force_blocks_default() ? fb : force_blocks_default());  // upper bound of the grid
     s->n_kin_blocks = 152 * 4;
     DevState &d = s->d;
     cudaError_t e = cudaMalloc((void **)&d.cell_count, sizeof(int) * ncell);

@@ -233,22 +233,33 @@ struct LaunchForce {
     template <class SIG>
     cudaError_t operator()() const
     {
-        if (half) {
-            const size_t sm = sizeof(typename ForceOp<SIG, true>::Tile) * MD_WARPS;
-            cudaFuncSetAttribute(k_force<SIG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            k_force<SIG, true><<<n_blocks, MD_WARPS * 32, sm, s>>>(A);
-        } else {
-            const size_t sm = sizeof(typename ForceOp<SIG, false>::Tile) * MD_WARPS;
-            cudaFuncSetAttribute(k_force<SIG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            k_force<SIG, false><<<n_blocks, MD_WARPS * 32, sm, s>>>(A);
-        }
+        if (half) return run<SIG, true>();
+        return run<SIG, false>();
+    }
+    // persistent grid: as many blocks as can be resident (grid-stride over
+    // cells), never more than the cells need nor than the partials hold
+    template <class SIG, bool HALF>
+    cudaError_t run() const
+    {
+        const size_t sm = sizeof(typename ForceOp<SIG, HALF>::Tile) * MD_WARPS;
+        cudaFuncSetAttribute(k_force<SIG, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<SIG, HALF>, MD_WARPS * 32, sm);
+        long long want = (long long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+        const long long need = (A.g.ncell + MD_WARPS - 1) / MD_WARPS;
+        if (want > need) want = need;
+        if (want > n_blocks) want = n_blocks;
+        if (want < 1) want = 1;
+        k_force<SIG, HALF><<<(unsigned)want, MD_WARPS * 32, sm, s>>>(A);
         return cudaGetLastError();
     }
 };
 
 }  // namespace
 
-int force_blocks_default() { return 152 * 4; }
+int force_blocks_default() { return 152 * 16; }
 
 cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half_shell, int n_blocks, cudaStream_t s)
 {
@@ -265,11 +276,14 @@ cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half
     A.n = d.n;
     A.partials = d.partials;
     A.flags = d.flags;
+    // the grid may be smaller than the partials buffer: unused slots read as 0
+    cudaError_t e = cudaMemsetAsync(d.partials, 0, sizeof(double) * P_COUNT * n_blocks, s);
+    if (e != cudaSuccess) return e;
     if (half_shell) {
-        cudaError_t e = cudaMemsetAsync(d.facc, 0, sizeof(float) * 6 * (d.n > 0 ? d.n : 1), s);
+        e = cudaMemsetAsync(d.facc, 0, sizeof(float) * 6 * (d.n > 0 ? d.n : 1), s);
         if (e != cudaSuccess) return e;
     }
-    cudaError_t e = dispatch_sig(m, LaunchForce{A, half_shell, n_blocks, s});
+    e = dispatch_sig(m, LaunchForce{A, half_shell, n_blocks, s});
     if (e != cudaSuccess || !half_shell || d.n == 0) return e;
     k_force_finalize<<<(unsigned)((d.n + 255) / 256), 256, 0, s>>>(d.facc, d.n, d.F, d.tau, d.flags);
     return cudaGetLastError();

@@ -50,8 +50,10 @@ constexpr unsigned SIG_2CLJQ = sigkey(ROLE_LJ, ROLE_LJ, ROLE_QUAD);
 constexpr unsigned SIG_2CLJDQ = sigkey(ROLE_LJ, ROLE_LJ, ROLE_DIP | ROLE_QUAD);
 constexpr unsigned SIG_4SITE = sigkey(ROLE_LJ, ROLE_LJ | ROLE_CHG, ROLE_LJ | ROLE_CHG, ROLE_DIP, ROLE_QUAD);
 
-// Compile-time site-role signature: S sites, 4 role bits per site.
-template <int S_, unsigned R_, bool SINGLE_ = false>
+// Compile-time site-role signature: S sites, 4 role bits per site, and the
+// LJ type of each LJ site (4 bits per site), so that the mixing-table
+// entries are compile-time constant-bank operands.
+template <int S_, unsigned R_, bool SINGLE_ = false, unsigned TY_ = 0>
 struct SigStatic {
     static constexpr int S = S_;
     static constexpr bool DYN = false;
@@ -59,6 +61,7 @@ struct SigStatic {
     static constexpr int K = S_ + sig_na(R_, S_);
     __device__ __forceinline__ static constexpr int role(int a, const DevModel &) { return sig_role(R_, a); }
     __device__ __forceinline__ static constexpr int slot(int a, const DevModel &) { return sig_slot(R_, a); }
+    __device__ __forceinline__ static constexpr int type(int a, const DevModel &) { return sig_role(TY_, a); }
     __device__ __forceinline__ static int kk(const DevModel &) { return K; }
     __device__ __forceinline__ static int s_of(const DevModel &) { return S_; }
 };
@@ -70,21 +73,28 @@ struct SigDyn {
     static constexpr bool SINGLE = false;
     __device__ __forceinline__ static int role(int a, const DevModel &m) { return a < m.S ? m.roles[a] : 0; }
     __device__ __forceinline__ static int slot(int a, const DevModel &m) { return m.axis_slot[a]; }
+    __device__ __forceinline__ static int type(int a, const DevModel &m) { return m.lj_type[a]; }
     __device__ __forceinline__ static int kk(const DevModel &m) { return m.S + m.NA; }
     __device__ __forceinline__ static int s_of(const DevModel &m) { return m.S; }
 };
+
+constexpr unsigned TY_4SITE = sigkey(0, 1, 1);  // LJ types of the 4-site model's sites
 
 // Dispatch of a model to its compiled signature: f.template operator()<SIG>().
 template <class F>
 __host__ auto dispatch_sig(const DevModel &m, F &&f)
 {
-    unsigned key = 0;
-    for (int a = 0; a < m.S; a++) key |= (unsigned)m.roles[a] << (4 * a);
-    if (m.single_lj_at_com) return f.template operator()<SigStatic<1, ROLE_LJ, true>>();
-    if (m.S == 2 && key == SIG_2CLJ) return f.template operator()<SigStatic<2, SIG_2CLJ>>();
-    if (m.S == 3 && key == SIG_2CLJQ) return f.template operator()<SigStatic<3, SIG_2CLJQ>>();
-    if (m.S == 3 && key == SIG_2CLJDQ) return f.template operator()<SigStatic<3, SIG_2CLJDQ>>();
-    if (m.S == 5 && key == SIG_4SITE) return f.template operator()<SigStatic<5, SIG_4SITE>>();
+    unsigned key = 0, ty = 0;
+    for (int a = 0; a < m.S; a++) {
+        key |= (unsigned)m.roles[a] << (4 * a);
+        if (m.roles[a] & ROLE_LJ) ty |= (unsigned)m.lj_type[a] << (4 * a);
+    }
+    if (m.single_lj_at_com && ty == 0) return f.template operator()<SigStatic<1, ROLE_LJ, true>>();
+    if (m.S == 2 && key == SIG_2CLJ && ty == 0) return f.template operator()<SigStatic<2, SIG_2CLJ>>();
+    if (m.S == 3 && key == SIG_2CLJQ && ty == 0) return f.template operator()<SigStatic<3, SIG_2CLJQ>>();
+    if (m.S == 3 && key == SIG_2CLJDQ && ty == 0) return f.template operator()<SigStatic<3, SIG_2CLJDQ>>();
+    if (m.S == 5 && key == SIG_4SITE && ty == TY_4SITE)
+        return f.template operator()<SigStatic<5, SIG_4SITE, false, TY_4SITE>>();
     return f.template operator()<SigDyn>();
 }
 
@@ -279,20 +289,27 @@ __device__ __forceinline__ void load_i(const DevModel &m, const float4 *com, con
 }
 
 // Pair of molecules: force on i, torque on i (lever arms + orientation),
-// torque on j (JSIDE), energy.  Site forces are summed per site of i inside
-// the pair so that the lever-arm torque costs 6 FMA per site of i.
+// energy; with JSIDE also the torque on j from the pair's angular-momentum
+// balance, tau_i + tau_j + X x F_ij = 0 (X = R_i - R_j), which holds exactly
+// for the rotation-invariant site-site laws of §2.  Site forces are summed
+// per site of i inside the pair so that the lever-arm torque costs 6 FMA
+// per site of i.
 template <class SIG, bool JSIDE>
 __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, const float X1, const float X2,
                                          const IMol<SIG> &I, const float4 *__restrict__ gj, float (&Fo)[3],
                                          float (&to)[3], float (&tj)[3], float &Uo)
 {
     constexpr int S = SIG::S;
-    float fa[S][3];
+    float fa[S][3], xa[S][3];
 #pragma unroll
-    for (int a = 0; a < S; a++) fa[a][0] = fa[a][1] = fa[a][2] = 0.f;
-    float ti[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < S; a++) {
+        fa[a][0] = fa[a][1] = fa[a][2] = 0.f;
+        xa[a][0] = X0 + I.d[a][0];
+        xa[a][1] = X1 + I.d[a][1];
+        xa[a][2] = X2 + I.d[a][2];
+    }
+    float ti[3] = {0.f, 0.f, 0.f}, tdummy[3];
     float U = 0.f;
-    tj[0] = tj[1] = tj[2] = 0.f;
     if (SIG::SINGLE) {
         const float r2 = X0 * X0 + X1 * X1 + X2 * X2;
         const float ir2 = __fdividef(1.f, r2);
@@ -311,16 +328,15 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
             const float4 db = __ldg(gj + b);
             float4 eb = make_float4(0.f, 0.f, 0.f, 0.f);
             if (rb & AX_ROLES) eb = __ldg(gj + SIG::s_of(m) + SIG::slot(b, m));
-            float fbx = 0.f, fby = 0.f, fbz = 0.f;
 #pragma unroll
             for (int a = 0; a < S; a++) {
                 const int ra = SIG::role(a, m);
                 const bool lj = (ra & ROLE_LJ) && (rb & ROLE_LJ);
                 const bool el = (ra & EL_ROLES) && (rb & EL_ROLES);
                 if (!lj && !el) continue;
-                const float x = X0 + I.d[a][0] - db.x;
-                const float y = X1 + I.d[a][1] - db.y;
-                const float z = X2 + I.d[a][2] - db.z;
+                const float x = xa[a][0] - db.x;
+                const float y = xa[a][1] - db.y;
+                const float z = xa[a][2] - db.z;
                 const float r2 = x * x + y * y + z * z;
                 float fx = 0.f, fy = 0.f, fz = 0.f;
                 float ir = 0.f, ir2;
@@ -331,7 +347,7 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
                     ir2 = __fdividef(1.f, r2);
                 }
                 if (lj) {
-                    const int ta = m.lj_type[a], tb = m.lj_type[b];
+                    const int ta = SIG::type(a, m), tb = SIG::type(b, m);
                     const float s2 = m.sig2[ta][tb] * ir2;
                     const float s6 = s2 * s2 * s2;
                     const float fr = m.eps24[ta][tb] * s6 * (2.f * s6 - 1.f) * ir2;
@@ -341,20 +357,12 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
                     fz = fr * z;
                 }
                 if (el) {
-                    elec_site<JSIDE>(ra, rb, m.chg[a], m.mu[a], m.Q[a], m.chg[b], m.mu[b], m.Q[b], m.frf, x, y, z,
-                                     ir, I.e[a], eb, U, fx, fy, fz, ti, tj);
+                    elec_site<false>(ra, rb, m.chg[a], m.mu[a], m.Q[a], m.chg[b], m.mu[b], m.Q[b], m.frf, x, y, z,
+                                     ir, I.e[a], eb, U, fx, fy, fz, ti, tdummy);
                 }
                 fa[a][0] += fx;
                 fa[a][1] += fy;
                 fa[a][2] += fz;
-                fbx += fx;
-                fby += fy;
-                fbz += fz;
-            }
-            if (JSIDE) {
-                tj[0] -= db.y * fbz - db.z * fby;
-                tj[1] -= db.z * fbx - db.x * fbz;
-                tj[2] -= db.x * fby - db.y * fbx;
             }
         }
     }
@@ -376,6 +384,15 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
     to[0] = ti[0];
     to[1] = ti[1];
     to[2] = ti[2];
+    if (JSIDE) {
+        if (SIG::SINGLE) {
+            tj[0] = tj[1] = tj[2] = 0.f;
+        } else {
+            tj[0] = -ti[0] - (X1 * F2 - X2 * F1);
+            tj[1] = -ti[1] - (X2 * F0 - X0 * F2);
+            tj[2] = -ti[2] - (X0 * F1 - X1 * F0);
+        }
+    }
     Uo = U;
 }
 
@@ -478,12 +495,11 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
                 const int skip_to = (self_n > 0 && HALF) ? max(0, min(self_n, il - self_lo + 1)) : 0;
                 const int self_k =
                     (self_n > 0 && !HALF && il >= self_lo && il < self_lo + self_n) ? self_base + (il - self_lo) : -1;
-                int qn = 0, nexam = 0;
+                int qn = 0;
                 for (int kb = skip_to; kb < nj; kb += 32) {
                     const int k = kb + lane;
                     bool hit = false;
                     if (k < nj && k != self_k) {
-                        nexam++;
                         const float4 cj = T.jc[k];
                         const float X0 = I.c.x - cj.x, X1 = I.c.y - cj.y, X2 = I.c.z - cj.z;
                         const float d2 = X0 * X0 + X1 * X1 + X2 * X2;
@@ -523,7 +539,7 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
                     }
                     __syncwarp();
                 }
-                op.count_examined(nexam);
+                if (lane == 0) op.count_examined(nj - skip_to - (self_k >= 0 ? 1 : 0));
                 op.i_end(I, il, lane);
             }
             __syncwarp();
