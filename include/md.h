@@ -206,6 +206,52 @@ md_status md_sync(md_system *sys, void *cuda_stream);
 md_status md_profile(md_system *sys, int32_t enable);
 md_status md_kernel_times_get(md_system *sys, md_kernel_times *out);
 
+/* ------------------------------------------------------------------------
+ * Batched replicas: n_sys independent systems of one model and cut-off,
+ * each with its own periodic box and molecules, advanced together.  One
+ * launch of each kernel covers every replica; the force kernels are
+ * persistent and take cells from a work queue ordered longest-first by the
+ * per-cell cost estimate n_d ~ N_i/2 (N_i + sum_neigh N_j) (§4, Eq. 6).
+ * Replicas with >= 3 cells per axis use the Newton-3 half stencil when
+ * options->half_shell is set, smaller boxes the full stencil.
+ *
+ * md_batch_create: boxes n_sys x 3 (host), each edge >= 2 cutoff.
+ * Errors as md_create. */
+md_status md_batch_create(int32_t n_sys, const double *boxes, double cutoff, const md_site_types *types,
+                          const md_options *options, md_batch **out);
+
+/* Molecules of all replicas, concatenated in replica order: n_per_sys[k]
+ * molecules of replica k (host array of n_sys); r, v, q, j as in
+ * md_set_molecules, sum(n_per_sys) rows each; v, j may be NULL. */
+md_status md_batch_set_molecules(md_batch *b, const int64_t *n_per_sys, const double *r, const double *v,
+                                 const double *q, const double *j, int32_t on_device, void *cuda_stream);
+
+/* Forces of every replica at the current configuration.  Asynchronous. */
+md_status md_batch_compute_forces(md_batch *b, void *cuda_stream);
+
+/* n_steps leapfrog steps (NVE) of every replica.  use_graph != 0 captures
+ * pairs of steps into a CUDA graph once (per buffer parity and dt) and
+ * replays it; an odd last step runs eagerly.  Asynchronous. */
+md_status md_batch_step(md_batch *b, int32_t n_steps, double dt, int32_t use_graph, void *cuda_stream);
+
+/* Observables of every replica (out: n_sys entries, host).  Synchronising. */
+md_status md_batch_energy_virial(md_batch *b, md_observables *out, void *cuda_stream);
+
+/* State / forces of all replicas in the concatenated input order. */
+md_status md_batch_get_molecules(md_batch *b, double *r, double *v, double *q, double *j, int32_t on_device,
+                                 void *cuda_stream);
+md_status md_batch_get_forces(md_batch *b, double *F, double *tau, int32_t on_device, void *cuda_stream);
+
+/* Autotuner: times the batched force evaluation for each work-chunk size
+ * (1, 2, 4, 8, 16 cells per queue grab) and grid occupancy (100% or 50% of
+ * the resident blocks) with CUDA events and keeps the fastest.  Outputs may
+ * be NULL.  Synchronising. */
+md_status md_batch_tune(md_batch *b, void *cuda_stream, int32_t *best_chunk, int32_t *best_grid_pct,
+                        float *best_ms);
+
+void md_batch_destroy(md_batch *b);
+const char *md_batch_last_error(const md_batch *b);
+
 /* Kinetic energies K_out[0] = sum 1/2 m v(t)^2 and K_out[1] = sum 1/2
  * w.I w at time t from half-step state, exactly as md_energy_virial forms
  * them (v(t) = v + dt/2 F/m, j(t) = j + dt/2 tau, w = I^-1 R(q)^T j(t)),

@@ -523,6 +523,15 @@ md_status do_force(md_system *s, cudaStream_t st)
 
 }  // namespace
 
+void model_info(const md_system *s, ModelInfo *out)
+{
+    out->m = s->m;
+    out->g = s->g;
+    out->lrc_u_coef = s->lrc_u_coef;
+    out->lrc_w_coef = s->lrc_w_coef;
+    out->rf_self_per_mol = s->rf_self_per_mol;
+}
+
 extern "C" {
 
 const char *md_status_str(md_status st)

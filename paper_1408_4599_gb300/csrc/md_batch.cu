@@ -1,0 +1,932 @@
+// md_batch.cu -- many independent replicas of uneven size advanced together
+// (one model, one cut-off, each replica its own periodic box and state).
+//
+// Layout: the replicas' molecules and linked cells are concatenated;
+// replica k owns slots [mol0_k, mol0_{k+1}) and cells [cell0_k, cell0_{k+1}).
+// The counting sort only permutes molecules inside their own cells, so the
+// slot -> replica map never changes.  One launch of each kernel covers all
+// replicas:
+//   integrate (per-slot replica box) -> one counting sort over all cells ->
+//   reorder + pack (per-slot replica grid) -> persistent force kernels.
+// The force kernels pull chunks of cells from an atomic work queue ordered
+// longest-first by the paper's per-cell cost estimate
+// n_d(i) ~ N_i/2 (N_i + sum_neigh N_j) (§4, Eq. 6), evaluated per replica
+// from its mean cell occupancy; replicas with >= 3 cells per axis use the
+// Newton-3 half stencil, smaller boxes the full stencil (two launches).
+// Energies and virials are written per cell and reduced per replica in a
+// fixed order.  md_batch_step can replay the steps from a captured CUDA
+// graph; md_batch_tune times the work-chunk size and grid occupancy.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "../../include/md.h"
+#include "md_forceop.cuh"
+
+using namespace mdk;
+
+// Per-replica grid on the device.
+struct RepGrid {
+    int nc[3];
+    int half;  // 1: half stencil
+    float ellf[3];
+    double L[3];
+    double ell[3];
+    long long cell0, mol0;
+};
+
+struct md_batch {
+    int n_sys = 0;
+    md_system *tmpl = nullptr;  // model compiled once (md_create of the first box)
+    DevModel m;
+    md_options opt;
+    double rc = 0.0, lrc_u = 0.0, lrc_w = 0.0, rf_self = 0.0;
+    std::vector<RepGrid> grids;
+    std::vector<long long> n_per;
+    std::vector<long long> cell_off;
+    long long ncell = 0, ntot = 0, cap = 0;
+    Grid g;  // shared scalars (rc2, band); ncell = total cells
+    DevState d;
+    RepGrid *dgrids = nullptr;
+    int *rep_of_slot = nullptr, *rep_of_cell = nullptr;
+    int *work = nullptr;  // [half list | full list] of cells, longest replicas first
+    long long n_work_half = 0, n_work_full = 0;
+    int *counters = nullptr;  // work-queue heads (2)
+    float *cellE = nullptr;   // 5 per cell
+    int *cellN = nullptr;     // 2 per cell
+    double *rep_obs = nullptr;  // 8 per replica
+    double *rep_kin = nullptr;  // 2 per replica
+    bool has_mol = false, forces_valid = false;
+    double dt_last = 0.0, time = 0.0;
+    long long step = 0;
+    int chunk = 2, grid_frac_pct = 100;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    double gdt[2] = {0.0, 0.0};
+    int parity = 0;
+    char err[512];
+};
+
+namespace {
+
+__device__ __forceinline__ int cell_axis_b(double x, double ell, int nc)
+{
+    int c = (int)floor(x / ell);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+__global__ void k_prepare_b(const RepGrid *G, const int *rep, double *r, double *q, int *ids, long long n, int *flags)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const RepGrid &g = G[rep[s]];
+    bool bad = false;
+    for (int k = 0; k < 3; k++) {
+        double x = r[3 * s + k];
+        bad |= !isfinite(x);
+        x -= g.L[k] * floor(x / g.L[k]);
+        if (x >= g.L[k]) x -= g.L[k];
+        if (x < 0.0) x = 0.0;
+        r[3 * s + k] = x;
+    }
+    double nn = sqrt(q[4 * s] * q[4 * s] + q[4 * s + 1] * q[4 * s + 1] + q[4 * s + 2] * q[4 * s + 2] +
+                     q[4 * s + 3] * q[4 * s + 3]);
+    bad |= !(nn > 0.0) || !isfinite(nn);
+    for (int k = 0; k < 4; k++) q[4 * s + k] /= nn;
+    ids[s] = (int)s;
+    if (bad) atomicExch(&flags[FLAG_NONFINITE], 1);
+}
+
+__global__ void k_cellid_b(const RepGrid *G, const int *rep, const double *r, int *cell, int *count, long long n)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const RepGrid &g = G[rep[s]];
+    const int cx = cell_axis_b(r[3 * s], g.ell[0], g.nc[0]);
+    const int cy = cell_axis_b(r[3 * s + 1], g.ell[1], g.nc[1]);
+    const int cz = cell_axis_b(r[3 * s + 2], g.ell[2], g.nc[2]);
+    const int c = (int)g.cell0 + (cz * g.nc[1] + cy) * g.nc[0] + cx;
+    cell[s] = c;
+    atomicAdd(&count[c], 1);
+}
+
+// Leapfrog of §3 (Eqs. 2-5) with the same precision split as the
+// single-system integrator; per-slot replica box for wrap and cell id.
+__device__ __forceinline__ void omega_b(const float q[4], const float j[3], const float Iinv[3], float w[3])
+{
+    const float qw = q[0], qx = q[1], qy = q[2], qz = q[3];
+    const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
+    const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
+    const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
+    w[0] = Iinv[0] * (R00 * j[0] + R10 * j[1] + R20 * j[2]);
+    w[1] = Iinv[1] * (R01 * j[0] + R11 * j[1] + R21 * j[2]);
+    w[2] = Iinv[2] * (R02 * j[0] + R12 * j[1] + R22 * j[2]);
+}
+
+__device__ __forceinline__ void qrate_b(const float q[4], const float w[3], float qd[4])
+{
+    qd[0] = 0.5f * (-q[1] * w[0] - q[2] * w[1] - q[3] * w[2]);
+    qd[1] = 0.5f * (q[0] * w[0] + q[2] * w[2] - q[3] * w[1]);
+    qd[2] = 0.5f * (q[0] * w[1] + q[3] * w[0] - q[1] * w[2]);
+    qd[3] = 0.5f * (q[0] * w[2] + q[1] * w[1] - q[2] * w[0]);
+}
+
+__global__ void k_integrate_b(const RepGrid *G, const int *rep, DevModel m, DevState d, double dt)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.n) return;
+    const RepGrid &g = G[rep[s]];
+    const double dtm = dt / m.mass;
+    int cc[3];
+    bool bad = false;
+    for (int k = 0; k < 3; k++) {
+        const double v = d.v[3 * s + k] + dtm * d.F[3 * s + k];
+        double r = d.r[3 * s + k] + dt * v;
+        bad |= !isfinite(r);
+        if (r < 0.0) r += g.L[k];
+        else if (r >= g.L[k]) r -= g.L[k];
+        if (!(r >= 0.0 && r < g.L[k])) {
+            r -= g.L[k] * floor(r / g.L[k]);
+            if (r >= g.L[k]) r -= g.L[k];
+            if (r < 0.0) r = 0.0;
+        }
+        d.v[3 * s + k] = v;
+        d.r[3 * s + k] = r;
+        cc[k] = cell_axis_b(r, g.ell[k], g.nc[k]);
+    }
+    if (m.rot_dof > 0) {
+        double q[4] = {d.q[4 * s], d.q[4 * s + 1], d.q[4 * s + 2], d.q[4 * s + 3]};
+        double j[3] = {d.j[3 * s], d.j[3 * s + 1], d.j[3 * s + 2]};
+        const double t[3] = {d.tau[3 * s], d.tau[3 * s + 1], d.tau[3 * s + 2]};
+        const float Iinv[3] = {(float)m.Iinv[0], (float)m.Iinv[1], (float)m.Iinv[2]};
+        const float hdt = (float)(0.5 * dt);
+        float qf[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
+        float jt[3], w[3], qd[4], qh[4], jh[3];
+        for (int k = 0; k < 3; k++) jt[k] = (float)j[k] + hdt * (float)t[k];
+        omega_b(qf, jt, Iinv, w);
+        qrate_b(qf, w, qd);
+        for (int k = 0; k < 4; k++) qh[k] = qf[k] + hdt * qd[k];
+        const float nh = rsqrtf(qh[0] * qh[0] + qh[1] * qh[1] + qh[2] * qh[2] + qh[3] * qh[3]);
+        for (int k = 0; k < 4; k++) qh[k] *= nh;
+        for (int k = 0; k < 3; k++) {
+            j[k] += dt * t[k];
+            jh[k] = (float)j[k];
+        }
+        omega_b(qh, jh, Iinv, w);
+        qrate_b(qh, w, qd);
+        for (int k = 0; k < 4; k++) q[k] += dt * (double)qd[k];
+        const double e = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3] - 1.0;
+        // (1 + e)^(-1/2): the cubic series is exact to FP64 rounding for |e| < 1e-4
+        const double inv = fabs(e) < 1e-4 ? 1.0 + e * (-0.5 + e * (0.375 - 0.3125 * e)) : 1.0 / sqrt(1.0 + e);
+        for (int k = 0; k < 4; k++) d.q[4 * s + k] = q[k] * inv;
+        for (int k = 0; k < 3; k++) d.j[3 * s + k] = j[k];
+        bad |= !isfinite(e);
+    }
+    if (bad) atomicExch(&d.flags[FLAG_NONFINITE], 1);
+    const int c = (int)g.cell0 + (cc[2] * g.nc[1] + cc[1]) * g.nc[0] + cc[0];
+    d.cell[s] = c;
+    atomicAdd(&d.cell_count[c], 1);
+}
+
+__global__ void k_reorder_pack_b(const RepGrid *G, const int *rep, DevModel m, DevState d)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.n) return;
+    const int o = d.perm2[s];
+    const double rx = d.r[3 * o], ry = d.r[3 * o + 1], rz = d.r[3 * o + 2];
+    d.r2[3 * s] = rx;
+    d.r2[3 * s + 1] = ry;
+    d.r2[3 * s + 2] = rz;
+    for (int k = 0; k < 3; k++) {
+        d.v2[3 * s + k] = d.v[3 * o + k];
+        d.j2[3 * s + k] = d.j[3 * o + k];
+    }
+    const double qw = d.q[4 * o], qx = d.q[4 * o + 1], qy = d.q[4 * o + 2], qz = d.q[4 * o + 3];
+    d.q2[4 * s] = qw;
+    d.q2[4 * s + 1] = qx;
+    d.q2[4 * s + 2] = qy;
+    d.q2[4 * s + 3] = qz;
+    d.ids2[s] = d.ids[o];
+    const RepGrid &g = G[rep[s]];
+    const int c = d.cell[o] - (int)g.cell0;
+    const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
+    d.com[s] = make_float4((float)(rx - (cx + 0.5) * g.ell[0]), (float)(ry - (cy + 0.5) * g.ell[1]),
+                           (float)(rz - (cz + 0.5) * g.ell[2]), 0.f);
+    if (m.single_lj_at_com) return;
+    const float w = (float)qw, x = (float)qx, y = (float)qy, z = (float)qz;
+    const float R[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
+                        2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
+                        2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
+    float4 *out = d.geo + s * (long long)d.K;
+    for (int a = 0; a < m.S; a++) {
+        const float *b = m.body[a];
+        out[a] = make_float4(R[0] * b[0] + R[1] * b[1] + R[2] * b[2], R[3] * b[0] + R[4] * b[1] + R[5] * b[2],
+                             R[6] * b[0] + R[7] * b[1] + R[8] * b[2], 0.f);
+        if (m.axis_slot[a] >= 0) {
+            const float *e = m.axis[a];
+            out[m.S + m.axis_slot[a]] =
+                make_float4(R[0] * e[0] + R[1] * e[1] + R[2] * e[2], R[3] * e[0] + R[4] * e[1] + R[5] * e[2],
+                            R[6] * e[0] + R[7] * e[1] + R[8] * e[2], 0.f);
+        }
+    }
+}
+
+struct BatchArgs {
+    ForceArgs f;  // model, packed data, accumulators (grid fields unused)
+    const RepGrid *grids;
+    const int *rep_of_cell;
+    const int *work;
+    long long n_work;
+    int *counter;
+    int chunk;
+    float *cellE;
+    int *cellN;
+};
+
+// Persistent force kernel over a work list of cells of many replicas.
+template <class SIG, bool HALF>
+__global__ void __launch_bounds__(MD_WARPS * 32) k_force_batch(const __grid_constant__ BatchArgs B)
+{
+    using Op = ForceOp<SIG, HALF>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    typename Op::Tile *T = reinterpret_cast<typename Op::Tile *>(smem_raw) + warp;
+    const DevModel &m = B.f.m;
+    const int K = SIG::kk(m);
+    Op op(m, B.f, K, T);
+    for (;;) {
+        long long w0 = 0;
+        if (lane == 0) w0 = atomicAdd(B.counter, B.chunk);
+        w0 = __shfl_sync(FULLMASK, w0, 0);
+        if (w0 >= B.n_work) break;
+        const long long w1 = min(w0 + (long long)B.chunk, B.n_work);
+        for (long long w = w0; w < w1; w++) {
+            const long long c = B.work[w];
+            const RepGrid &rg = B.grids[B.rep_of_cell[c]];
+            GridView gv;
+            for (int k = 0; k < 3; k++) {
+                gv.nc[k] = rg.nc[k];
+                gv.ellf[k] = rg.ellf[k];
+                gv.L[k] = rg.L[k];
+            }
+            gv.rc2 = B.f.g.rc2;
+            gv.rc2f = B.f.g.rc2f;
+            gv.bandf = B.f.g.bandf;
+            gv.cell0 = rg.cell0;
+            traverse_cell<SIG, HALF>(m, gv, B.f.cell_start, B.f.com, B.f.geo, B.f.r, K, c - rg.cell0, *T, op, lane);
+            float v[5];
+            int nm, ne;
+            op_warp_totals(op, v, nm, ne);
+            if (lane == 0) {
+                for (int q = 0; q < 5; q++) B.cellE[5 * c + q] = v[q];
+                B.cellN[2 * c] = nm;
+                B.cellN[2 * c + 1] = ne;
+            }
+            op.sU = op.kU = op.sW = op.kW = op.sX = op.kX = op.sY = op.kY = op.sZ = op.kZ = 0.f;
+            op.nmol = op.nexam = 0;
+        }
+    }
+}
+
+// One block per replica: energies/virials/counts (fixed summation order).
+__global__ void k_rep_reduce(const RepGrid *G, int n_sys, long long ncell, const float *cellE, const int *cellN,
+                             int site_pairs, double *out)
+{
+    const int k = blockIdx.x;
+    if (k >= n_sys) return;
+    const long long c0 = G[k].cell0, c1 = (k + 1 < n_sys) ? G[k + 1].cell0 : ncell;
+    __shared__ double sh[8][32];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        for (int q = 0; q < 5; q++) acc[q] += (double)cellE[5 * c + q];
+        acc[5] += (double)cellN[2 * c];
+        acc[7] += (double)cellN[2 * c + 1];
+    }
+    for (int q = 0; q < 8; q++)
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int q = 0; q < 8; q++) sh[q][warp] = acc[q];
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[threadIdx.x][w];
+        const double esc = G[k].half ? 1.0 : 0.5;
+        if (threadIdx.x == 6) {
+            t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[5][w];
+            t *= (double)site_pairs;
+        }
+        out[8 * k + threadIdx.x] = esc * t;
+    }
+}
+
+// One block per replica: kinetic energies at integer time (FP64).
+__global__ void k_rep_kinetic(const RepGrid *G, int n_sys, long long n, DevModel m, DevState d, double dt_half,
+                              double *out)
+{
+    const int k = blockIdx.x;
+    if (k >= n_sys) return;
+    const long long s0 = G[k].mol0, s1 = (k + 1 < n_sys) ? G[k + 1].mol0 : n;
+    __shared__ double sh[2][32];
+    double kt = 0.0, kr = 0.0;
+    const double im = 1.0 / m.mass;
+    for (long long s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        double v2 = 0.0;
+        for (int q = 0; q < 3; q++) {
+            const double vq = d.v[3 * s + q] + dt_half * d.F[3 * s + q] * im;
+            v2 += vq * vq;
+        }
+        kt += 0.5 * m.mass * v2;
+        if (m.rot_dof > 0) {
+            const double qw = d.q[4 * s], qx = d.q[4 * s + 1], qy = d.q[4 * s + 2], qz = d.q[4 * s + 3];
+            double jt[3];
+            for (int q = 0; q < 3; q++) jt[q] = d.j[3 * s + q] + dt_half * d.tau[3 * s + q];
+            const double R00 = 1 - 2 * (qy * qy + qz * qz), R01 = 2 * (qx * qy - qw * qz), R02 = 2 * (qx * qz + qw * qy);
+            const double R10 = 2 * (qx * qy + qw * qz), R11 = 1 - 2 * (qx * qx + qz * qz), R12 = 2 * (qy * qz - qw * qx);
+            const double R20 = 2 * (qx * qz - qw * qy), R21 = 2 * (qy * qz + qw * qx), R22 = 1 - 2 * (qx * qx + qy * qy);
+            const double w0 = m.Iinv[0] * (R00 * jt[0] + R10 * jt[1] + R20 * jt[2]);
+            const double w1 = m.Iinv[1] * (R01 * jt[0] + R11 * jt[1] + R21 * jt[2]);
+            const double w2 = m.Iinv[2] * (R02 * jt[0] + R12 * jt[1] + R22 * jt[2]);
+            kr += 0.5 * (m.I[0] * w0 * w0 + m.I[1] * w1 * w1 + m.I[2] * w2 * w2);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        kt += __shfl_xor_sync(0xffffffffu, kt, o);
+        kr += __shfl_xor_sync(0xffffffffu, kr, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][warp] = kt;
+        sh[1][warp] = kr;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[threadIdx.x][w];
+        out[2 * k + threadIdx.x] = t;
+    }
+}
+
+struct LaunchBatchForce {
+    const BatchArgs &B;
+    int half, blocks_cap;
+    cudaStream_t s;
+    template <class SIG>
+    cudaError_t operator()() const
+    {
+        if (half) return run<SIG, true>();
+        return run<SIG, false>();
+    }
+    template <class SIG, bool HALF>
+    cudaError_t run() const
+    {
+        if (B.n_work == 0) return cudaSuccess;
+        const size_t sm = sizeof(typename ForceOp<SIG, HALF>::Tile) * MD_WARPS;
+        cudaFuncSetAttribute(k_force_batch<SIG, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        int per_sm = 0, dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_batch<SIG, HALF>, MD_WARPS * 32, sm);
+        long long want = (long long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+        want = want * blocks_cap / 100;
+        const long long need = (B.n_work + MD_WARPS - 1) / MD_WARPS;
+        if (want > need) want = need;
+        if (want < 1) want = 1;
+        k_force_batch<SIG, HALF><<<(unsigned)want, MD_WARPS * 32, sm, s>>>(B);
+        return cudaGetLastError();
+    }
+};
+
+void bset_err(md_batch *b, const char *msg) { snprintf(b->err, sizeof b->err, "%s", msg); }
+
+md_status bcuda(md_batch *b, cudaError_t e, const char *where)
+{
+    snprintf(b->err, sizeof b->err, "%s: %s", where, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MD_ERR_OOM : MD_ERR_CUDA;
+}
+
+#define BCK(call, where)                                      \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return bcuda(b, e_, where);    \
+    } while (0)
+
+inline unsigned nb256(long long n) { return (unsigned)((n + 255) / 256); }
+
+BatchArgs batch_args(md_batch *b, bool half_list)
+{
+    BatchArgs B;
+    memset(&B, 0, sizeof B);
+    B.f.g = b->g;
+    B.f.m = b->m;
+    B.f.cell_start = b->d.cell_start;
+    B.f.com = b->d.com;
+    B.f.geo = b->d.geo;
+    B.f.r = b->d.r;
+    B.f.F = b->d.F;
+    B.f.tau = b->d.tau;
+    B.f.acc = b->d.facc;
+    B.f.n = b->d.n;
+    B.f.partials = nullptr;
+    B.f.flags = b->d.flags;
+    B.f.to_acc = 1;
+    B.grids = b->dgrids;
+    B.rep_of_cell = b->rep_of_cell;
+    B.work = half_list ? b->work : b->work + b->n_work_half;
+    B.n_work = half_list ? b->n_work_half : b->n_work_full;
+    B.counter = b->counters + (half_list ? 0 : 1);
+    B.chunk = b->chunk;
+    B.cellE = b->cellE;
+    B.cellN = b->cellN;
+    return B;
+}
+
+// Forces for all replicas at the current (packed) configuration.
+md_status batch_force(md_batch *b, cudaStream_t st)
+{
+    DevState &d = b->d;
+    BCK(cudaMemsetAsync(d.facc, 0, sizeof(float) * 6 * (d.n > 0 ? d.n : 1), st), "zero accumulators");
+    BCK(cudaMemsetAsync(b->counters, 0, 2 * sizeof(int), st), "zero work queues");
+    for (int h = 1; h >= 0; h--) {
+        BatchArgs B = batch_args(b, h == 1);
+        BCK(dispatch_sig(b->m, LaunchBatchForce{B, h, b->grid_frac_pct, st}), "batched force kernel");
+    }
+    BCK(launch_force_finalize(d, st), "force finalize");
+    b->forces_valid = true;
+    return MD_OK;
+}
+
+md_status batch_rebuild(md_batch *b, cudaStream_t st, bool need_cellid)
+{
+    DevState &d = b->d;
+    if (need_cellid) {
+        BCK(cudaMemsetAsync(d.cell_count, 0, sizeof(int) * b->ncell, st), "zero counts");
+        if (d.n > 0) k_cellid_b<<<nb256(d.n), 256, 0, st>>>(b->dgrids, b->rep_of_slot, d.r, d.cell, d.cell_count, d.n);
+    }
+    BCK(launch_sort(b->ncell, d, st), "counting sort");
+    if (d.n > 0) k_reorder_pack_b<<<nb256(d.n), 256, 0, st>>>(b->dgrids, b->rep_of_slot, b->m, d);
+    BCK(cudaGetLastError(), "reorder/pack kernel");
+    swap_state(d);
+    return MD_OK;
+}
+
+md_status batch_one_step(md_batch *b, double dt, cudaStream_t st)
+{
+    DevState &d = b->d;
+    BCK(cudaMemsetAsync(d.cell_count, 0, sizeof(int) * b->ncell, st), "zero counts");
+    if (d.n > 0) k_integrate_b<<<nb256(d.n), 256, 0, st>>>(b->dgrids, b->rep_of_slot, b->m, d, dt);
+    BCK(cudaGetLastError(), "integrate kernel");
+    md_status ms = batch_rebuild(b, st, false);
+    if (ms != MD_OK) return ms;
+    return batch_force(b, st);
+}
+
+void drop_graphs(md_batch *b)
+{
+    for (int p = 0; p < 2; p++)
+        if (b->gexec[p]) {
+            cudaGraphExecDestroy(b->gexec[p]);
+            b->gexec[p] = nullptr;
+        }
+}
+
+void batch_free(md_batch *b)
+{
+    drop_graphs(b);
+    DevState &d = b->d;
+    void *ptrs[] = {d.r, d.v, d.q, d.j, d.r2, d.v2, d.q2, d.j2, d.ids, d.ids2, d.F, d.tau, d.cell, d.cell_count,
+                    d.cell_start, d.cell_fill, d.perm, d.perm2, d.com, d.geo, d.scan_tmp, d.flags, d.facc,
+                    b->dgrids, b->rep_of_slot, b->rep_of_cell, b->work, b->counters, b->cellE, b->cellN,
+                    b->rep_obs, b->rep_kin};
+    for (void *p : ptrs) cudaFree(p);
+    memset(&b->d, 0, sizeof b->d);
+    b->dgrids = nullptr;
+    b->rep_of_slot = b->rep_of_cell = b->work = b->counters = b->cellN = nullptr;
+    b->cellE = nullptr;
+    b->rep_obs = b->rep_kin = nullptr;
+    b->cap = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+md_status md_batch_create(int32_t n_sys, const double *boxes, double cutoff, const md_site_types *types,
+                          const md_options *options, md_batch **out)
+{
+    if (!out || n_sys < 1 || !boxes || !types) return MD_ERR_ARG;
+    *out = nullptr;
+    md_batch *b = new (std::nothrow) md_batch();
+    if (!b) return MD_ERR_OOM;
+    for (int k = 0; k < n_sys; k++)
+        for (int a = 0; a < 3; a++)
+            if (!(std::isfinite(boxes[3 * k + a]) && boxes[3 * k + a] > 0.0)) {
+                delete b;
+                return MD_ERR_ARG;
+            } else if (boxes[3 * k + a] < 2.0 * cutoff) {
+                delete b;
+                return MD_ERR_BOX;
+            }
+    md_options opt = {INFINITY, 0, 0, 1, 1};
+    if (options) opt = *options;
+    md_status st = md_create(boxes, cutoff, types, &opt, &b->tmpl);
+    if (st != MD_OK) {
+        delete b;
+        return st;
+    }
+    ModelInfo mi;
+    model_info(b->tmpl, &mi);
+    b->m = mi.m;
+    b->g = mi.g;
+    b->lrc_u = mi.lrc_u_coef;
+    b->lrc_w = mi.lrc_w_coef;
+    b->rf_self = mi.rf_self_per_mol;
+    b->opt = opt;
+    b->rc = cutoff;
+    b->n_sys = n_sys;
+    b->grids.resize(n_sys);
+    b->cell_off.assign(n_sys + 1, 0);
+    long long nc_tot = 0;
+    for (int k = 0; k < n_sys; k++) {
+        RepGrid &g = b->grids[k];
+        bool all3 = true;
+        for (int a = 0; a < 3; a++) {
+            int nc = (int)std::floor(boxes[3 * k + a] / (cutoff * (1.0 + 1e-9)));
+            g.nc[a] = nc < 1 ? 1 : nc;
+            g.L[a] = boxes[3 * k + a];
+            g.ell[a] = g.L[a] / g.nc[a];
+            g.ellf[a] = (float)g.ell[a];
+            all3 = all3 && g.nc[a] >= 3;
+        }
+        g.half = (opt.half_shell && all3) ? 1 : 0;
+        g.cell0 = nc_tot;
+        b->cell_off[k] = nc_tot;
+        nc_tot += (long long)g.nc[0] * g.nc[1] * g.nc[2];
+    }
+    b->cell_off[n_sys] = nc_tot;
+    if (nc_tot > (1LL << 31) - 2) {
+        md_destroy(b->tmpl);
+        delete b;
+        return MD_ERR_UNSUPPORTED;
+    }
+    b->ncell = nc_tot;
+    b->g.ncell = nc_tot;
+    b->d.K = b->m.single_lj_at_com ? 0 : b->m.S + b->m.NA;
+    DevState &d = b->d;
+    cudaError_t e = cudaMalloc((void **)&d.cell_count, sizeof(int) * nc_tot);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.cell_start, sizeof(int) * (nc_tot + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.cell_fill, sizeof(int) * nc_tot);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.scan_tmp, sizeof(int) * (scan_blocks(nc_tot) + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.flags, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(d.flags, 0, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(d.cell_start, 0, sizeof(int) * (nc_tot + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->dgrids, sizeof(RepGrid) * n_sys);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->rep_of_cell, sizeof(int) * nc_tot);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->work, sizeof(int) * nc_tot);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->counters, sizeof(int) * 2);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->cellE, sizeof(float) * 5 * nc_tot);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->cellN, sizeof(int) * 2 * nc_tot);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->rep_obs, sizeof(double) * 8 * n_sys);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->rep_kin, sizeof(double) * 2 * n_sys);
+    if (e == cudaSuccess) e = cudaMemset(b->cellE, 0, sizeof(float) * 5 * nc_tot);
+    if (e == cudaSuccess) e = cudaMemset(b->cellN, 0, sizeof(int) * 2 * nc_tot);
+    if (e == cudaSuccess) {
+        std::vector<int> roc(nc_tot);
+        for (int k = 0; k < n_sys; k++)
+            for (long long c = b->cell_off[k]; c < b->cell_off[k + 1]; c++) roc[c] = k;
+        e = cudaMemcpy(b->rep_of_cell, roc.data(), sizeof(int) * nc_tot, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        md_status r = bcuda(b, e, "md_batch_create allocations");
+        batch_free(b);
+        md_destroy(b->tmpl);
+        delete b;
+        return r;
+    }
+    *out = b;
+    return MD_OK;
+}
+
+void md_batch_destroy(md_batch *b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    batch_free(b);
+    md_destroy(b->tmpl);
+    delete b;
+}
+
+const char *md_batch_last_error(const md_batch *b) { return b ? b->err : "NULL handle"; }
+
+md_status md_batch_set_molecules(md_batch *b, const int64_t *n_per_sys, const double *r, const double *v,
+                                 const double *q, const double *j, int32_t on_device, void *cuda_stream)
+{
+    if (!b || !n_per_sys) return MD_ERR_ARG;
+    long long ntot = 0;
+    for (int k = 0; k < b->n_sys; k++) {
+        if (n_per_sys[k] < 0) return MD_ERR_ARG;
+        ntot += n_per_sys[k];
+    }
+    if (ntot > (1LL << 31) - 1 || (ntot > 0 && (!r || !q))) return MD_ERR_ARG;
+    if (!on_device)
+        for (long long i = 0; i < 3 * ntot; i++)
+            if (!std::isfinite(r[i]) || (v && !std::isfinite(v[i])) || (j && !std::isfinite(j[i]))) {
+                bset_err(b, "md_batch_set_molecules: non-finite input");
+                return MD_ERR_ARG;
+            }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    drop_graphs(b);
+    DevState &d = b->d;
+    if (ntot > b->cap || !d.r) {
+        double **dbl[] = {&d.r, &d.v, &d.j, &d.r2, &d.v2, &d.j2, &d.F, &d.tau};
+        for (auto p : dbl) {
+            cudaFree(*p);
+            *p = nullptr;
+        }
+        void *others[] = {d.q, d.q2, d.ids, d.ids2, d.cell, d.perm, d.perm2, d.com, d.geo, d.facc, b->rep_of_slot};
+        for (void *p : others) cudaFree(p);
+        d.q = d.q2 = nullptr;
+        d.ids = d.ids2 = d.cell = d.perm = d.perm2 = nullptr;
+        d.com = d.geo = nullptr;
+        d.facc = nullptr;
+        b->rep_of_slot = nullptr;
+        const size_t nn = (size_t)(ntot > 0 ? ntot : 1);
+        cudaError_t e = cudaSuccess;
+        for (auto p : dbl)
+            if (e == cudaSuccess) e = cudaMalloc((void **)p, nn * 3 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&d.q, nn * 4 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&d.q2, nn * 4 * sizeof(double));
+        int **ints[] = {&d.ids, &d.ids2, &d.cell, &d.perm, &d.perm2, &b->rep_of_slot};
+        for (auto p : ints)
+            if (e == cudaSuccess) e = cudaMalloc((void **)p, nn * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&d.com, nn * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&d.geo, nn * (size_t)(d.K > 0 ? d.K : 1) * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&d.facc, nn * 6 * sizeof(float));
+        if (e != cudaSuccess) return bcuda(b, e, "allocating batch molecule buffers");
+        b->cap = ntot;
+    }
+    d.n = ntot;
+    b->ntot = ntot;
+    b->n_per.assign(n_per_sys, n_per_sys + b->n_sys);
+    // per-replica molecule offsets and the longest-first work list
+    long long m0 = 0;
+    std::vector<int> ros((size_t)(ntot > 0 ? ntot : 1));
+    std::vector<double> cost(b->n_sys);
+    for (int k = 0; k < b->n_sys; k++) {
+        RepGrid &g = b->grids[k];
+        g.mol0 = m0;
+        for (long long i = 0; i < n_per_sys[k]; i++) ros[m0 + i] = k;
+        m0 += n_per_sys[k];
+        const double nce = (double)(b->cell_off[k + 1] - b->cell_off[k]);
+        const double occ = (double)n_per_sys[k] / nce;  // mean molecules per cell
+        cost[k] = nce * 0.5 * occ * (occ + 26.0 * occ);  // sum over cells of n_d (§4, Eq. 6)
+    }
+    std::vector<int> order(b->n_sys);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+    std::vector<int> wl;
+    wl.reserve((size_t)b->ncell);
+    for (int pass = 1; pass >= 0; pass--)
+        for (int k : order)
+            if (b->grids[k].half == pass)
+                for (long long c = b->cell_off[k]; c < b->cell_off[k + 1]; c++) wl.push_back((int)c);
+    b->n_work_half = 0;
+    for (int k = 0; k < b->n_sys; k++)
+        if (b->grids[k].half) b->n_work_half += b->cell_off[k + 1] - b->cell_off[k];
+    b->n_work_full = b->ncell - b->n_work_half;
+    cudaStream_t st0 = st;
+    BCK(cudaMemcpyAsync(b->dgrids, b->grids.data(), sizeof(RepGrid) * b->n_sys, cudaMemcpyHostToDevice, st0),
+        "copy grids");
+    BCK(cudaMemcpyAsync(b->work, wl.data(), sizeof(int) * wl.size(), cudaMemcpyHostToDevice, st0), "copy work list");
+    BCK(cudaMemcpyAsync(b->rep_of_slot, ros.data(), sizeof(int) * ros.size(), cudaMemcpyHostToDevice, st0),
+        "copy slot map");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t b3 = sizeof(double) * 3 * (size_t)ntot, b4 = sizeof(double) * 4 * (size_t)ntot;
+    if (ntot > 0) {
+        BCK(cudaMemcpyAsync(d.r, r, b3, kind, st), "copy r");
+        BCK(cudaMemcpyAsync(d.q, q, b4, kind, st), "copy q");
+        if (v) BCK(cudaMemcpyAsync(d.v, v, b3, kind, st), "copy v");
+        else BCK(cudaMemsetAsync(d.v, 0, b3, st), "zero v");
+        if (j) BCK(cudaMemcpyAsync(d.j, j, b3, kind, st), "copy j");
+        else BCK(cudaMemsetAsync(d.j, 0, b3, st), "zero j");
+        BCK(cudaMemsetAsync(d.F, 0, b3, st), "zero F");
+        BCK(cudaMemsetAsync(d.tau, 0, b3, st), "zero tau");
+        k_prepare_b<<<nb256(ntot), 256, 0, st>>>(b->dgrids, b->rep_of_slot, d.r, d.q, d.ids, ntot, d.flags);
+        BCK(cudaGetLastError(), "prepare kernel");
+    }
+    md_status ms = batch_rebuild(b, st, true);
+    if (ms != MD_OK) return ms;
+    b->has_mol = true;
+    b->forces_valid = false;
+    b->dt_last = b->time = 0.0;
+    b->step = 0;
+    b->parity = 0;
+    if (!on_device) BCK(cudaStreamSynchronize(st), "md_batch_set_molecules sync");
+    return MD_OK;
+}
+
+md_status md_batch_compute_forces(md_batch *b, void *cuda_stream)
+{
+    if (!b) return MD_ERR_ARG;
+    if (!b->has_mol) {
+        bset_err(b, "md_batch_compute_forces: call md_batch_set_molecules first");
+        return MD_ERR_STATE;
+    }
+    return batch_force(b, (cudaStream_t)cuda_stream);
+}
+
+md_status md_batch_step(md_batch *b, int32_t n_steps, double dt, int32_t use_graph, void *cuda_stream)
+{
+    if (!b) return MD_ERR_ARG;
+    if (!b->has_mol) {
+        bset_err(b, "md_batch_step: call md_batch_set_molecules first");
+        return MD_ERR_STATE;
+    }
+    if (n_steps < 0 || !std::isfinite(dt) || !(dt > 0.0) || !(b->m.mass > 0.0)) return MD_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (!b->forces_valid) {
+        md_status ms = batch_force(b, st);
+        if (ms != MD_OK) return ms;
+    }
+    int k = 0;
+    if (use_graph) {
+        // a captured pair of steps returns the ping-pong buffers to where they
+        // started, so one executable graph per buffer parity is replayed
+        for (; k + 2 <= n_steps; k += 2) {
+            const int p = b->parity;
+            if (!b->gexec[p] || b->gdt[p] != dt) {
+                if (b->gexec[p]) cudaGraphExecDestroy(b->gexec[p]);
+                b->gexec[p] = nullptr;
+                cudaStream_t cs;
+                BCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+                cudaGraph_t graph;
+                BCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+                DevState saved = b->d;
+                md_status ms = batch_one_step(b, dt, cs);
+                if (ms == MD_OK) ms = batch_one_step(b, dt, cs);
+                cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+                b->d = saved;  // the capture only recorded; the state has not moved
+                cudaStreamDestroy(cs);
+                if (ms != MD_OK) return ms;
+                BCK(ec, "end capture");
+                cudaError_t ei = cudaGraphInstantiate(&b->gexec[p], graph, 0);
+                cudaGraphDestroy(graph);
+                BCK(ei, "graph instantiate");
+                b->gdt[p] = dt;
+            }
+            BCK(cudaGraphLaunch(b->gexec[p], st), "graph launch");
+            // two swaps: the buffer assignment is back where it started
+        }
+    }
+    for (; k < n_steps; k++) {
+        md_status ms = batch_one_step(b, dt, st);
+        if (ms != MD_OK) return ms;
+        b->parity ^= 1;
+    }
+    b->step += n_steps;
+    b->time += n_steps * dt;
+    b->dt_last = dt;
+    b->forces_valid = true;
+    return MD_OK;
+}
+
+md_status md_batch_energy_virial(md_batch *b, md_observables *out, void *cuda_stream)
+{
+    if (!b || !out) return MD_ERR_ARG;
+    if (!b->forces_valid) {
+        bset_err(b, "md_batch_energy_virial: no force evaluation yet");
+        return MD_ERR_STATE;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    DevState &d = b->d;
+    k_rep_reduce<<<b->n_sys, 256, 0, st>>>(b->dgrids, b->n_sys, b->ncell, b->cellE, b->cellN,
+                                            b->m.site_pairs_per_mol_pair, b->rep_obs);
+    k_rep_kinetic<<<b->n_sys, 256, 0, st>>>(b->dgrids, b->n_sys, d.n, b->m, d, 0.5 * b->dt_last, b->rep_kin);
+    BCK(cudaGetLastError(), "replica reductions");
+    std::vector<double> ob(8 * b->n_sys), kn(2 * b->n_sys);
+    int fl[4];
+    BCK(cudaMemcpyAsync(ob.data(), b->rep_obs, ob.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "copy obs");
+    BCK(cudaMemcpyAsync(kn.data(), b->rep_kin, kn.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "copy kin");
+    BCK(cudaMemcpyAsync(fl, d.flags, sizeof fl, cudaMemcpyDeviceToHost, st), "copy flags");
+    BCK(cudaStreamSynchronize(st), "md_batch_energy_virial sync");
+    for (int k = 0; k < b->n_sys; k++) {
+        md_observables &o = out[k];
+        memset(&o, 0, sizeof o);
+        const RepGrid &g = b->grids[k];
+        const double N = (double)b->n_per[k], V = g.L[0] * g.L[1] * g.L[2];
+        o.U_pot = ob[8 * k + P_U];
+        o.W = ob[8 * k + P_W];
+        o.W_xx = ob[8 * k + P_WXX];
+        o.W_yy = ob[8 * k + P_WYY];
+        o.W_zz = ob[8 * k + P_WZZ];
+        o.n_mol_pairs = (int64_t)llround(ob[8 * k + P_NMOL]);
+        o.n_site_pairs = (int64_t)llround(ob[8 * k + P_NSITE]);
+        o.n_examined = (int64_t)llround(ob[8 * k + P_NEXAM]);
+        o.U_lrc = b->opt.lj_lrc ? b->lrc_u * N * N / V : 0.0;
+        o.W_lrc = b->opt.lj_lrc ? b->lrc_w * N * N / V : 0.0;
+        o.U_rf_self = b->rf_self * N;
+        o.K_trans = kn[2 * k];
+        o.K_rot = kn[2 * k + 1];
+        const double dof = 3.0 * N - 3.0 + (double)b->m.rot_dof * N;
+        o.T = dof > 0 ? 2.0 * (o.K_trans + o.K_rot) / dof : 0.0;
+        o.P = (2.0 * o.K_trans + o.W + o.W_lrc) / (3.0 * V);
+        o.time = b->time;
+        o.step = b->step;
+        o.n_molecules = b->n_per[k];
+    }
+    if (fl[FLAG_NONFINITE]) {
+        bset_err(b, "non-finite force, torque or position detected on the device");
+        return MD_ERR_NONFINITE;
+    }
+    return MD_OK;
+}
+
+md_status md_batch_get_molecules(md_batch *b, double *r, double *v, double *q, double *j, int32_t on_device,
+                                 void *cuda_stream)
+{
+    if (!b) return MD_ERR_ARG;
+    if (!b->has_mol) return MD_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    DevState &d = b->d;
+    const double *src[4] = {d.r, d.v, d.q, d.j};
+    double *dst[4] = {r, v, q, j}, *tmp[4] = {d.r2, d.v2, d.q2, d.j2};
+    const int w[4] = {3, 3, 4, 3};
+    for (int k = 0; k < 4; k++) {
+        if (!dst[k] || d.n == 0) continue;
+        BCK(launch_scatter_out(d, src[k], w[k], on_device ? dst[k] : tmp[k], st), "scatter kernel");
+        if (!on_device)
+            BCK(cudaMemcpyAsync(dst[k], tmp[k], sizeof(double) * w[k] * (size_t)d.n, cudaMemcpyDeviceToHost, st),
+                "copy to host");
+    }
+    BCK(cudaStreamSynchronize(st), "md_batch_get_molecules sync");
+    return MD_OK;
+}
+
+md_status md_batch_get_forces(md_batch *b, double *F, double *tau, int32_t on_device, void *cuda_stream)
+{
+    if (!b) return MD_ERR_ARG;
+    if (!b->forces_valid) return MD_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    DevState &d = b->d;
+    const double *src[2] = {d.F, d.tau};
+    double *dst[2] = {F, tau}, *tmp[2] = {d.r2, d.v2};
+    for (int k = 0; k < 2; k++) {
+        if (!dst[k] || d.n == 0) continue;
+        BCK(launch_scatter_out(d, src[k], 3, on_device ? dst[k] : tmp[k], st), "scatter kernel");
+        if (!on_device)
+            BCK(cudaMemcpyAsync(dst[k], tmp[k], sizeof(double) * 3 * (size_t)d.n, cudaMemcpyDeviceToHost, st),
+                "copy to host");
+    }
+    BCK(cudaStreamSynchronize(st), "md_batch_get_forces sync");
+    return MD_OK;
+}
+
+// Times the batched force evaluation for each (work-chunk size, grid
+// occupancy) candidate with CUDA events and keeps the fastest.
+md_status md_batch_tune(md_batch *b, void *cuda_stream, int32_t *best_chunk, int32_t *best_grid_pct, float *best_ms)
+{
+    if (!b) return MD_ERR_ARG;
+    if (!b->has_mol) return MD_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int chunks[] = {1, 2, 4, 8, 16};
+    const int grids[] = {100, 50};
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0), "event");
+    BCK(cudaEventCreate(&e1), "event");
+    float best = 1e30f;
+    int bc = b->chunk, bg = b->grid_frac_pct;
+    md_status ms = batch_force(b, st);  // warm-up
+    for (int gi = 0; gi < 2 && ms == MD_OK; gi++)
+        for (int ci = 0; ci < 5 && ms == MD_OK; ci++) {
+            b->chunk = chunks[ci];
+            b->grid_frac_pct = grids[gi];
+            cudaEventRecord(e0, st);
+            for (int rep = 0; rep < 3 && ms == MD_OK; rep++) ms = batch_force(b, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            t /= 3.f;
+            if (t < best) {
+                best = t;
+                bc = chunks[ci];
+                bg = grids[gi];
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->chunk = bc;
+    b->grid_frac_pct = bg;
+    drop_graphs(b);
+    if (best_chunk) *best_chunk = bc;
+    if (best_grid_pct) *best_grid_pct = bg;
+    if (best_ms) *best_ms = best;
+    return ms;
+}
+
+}  // extern "C"

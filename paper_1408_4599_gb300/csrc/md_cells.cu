@@ -255,21 +255,41 @@ cudaError_t launch_cellid(const Grid &g, DevState &d, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Counting sort over ncell cells: scan of the histogram, scatter and the
+// in-cell sort; leaves the new order (new slot -> old slot) in perm2.
+cudaError_t launch_sort(long long ncell, DevState &d, cudaStream_t s)
+{
+    int nb = scan_blocks(ncell);
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(d.cell_count, ncell, d.scan_tmp);
+    k_scan_top<<<1, SCAN_THREADS, 0, s>>>(d.scan_tmp, nb);
+    k_scan_down<<<nb, SCAN_THREADS, 0, s>>>(d.cell_count, ncell, d.scan_tmp, d.cell_start);
+    cudaError_t e = cudaMemsetAsync(d.cell_fill, 0, sizeof(int) * ncell, s);
+    if (e != cudaSuccess) return e;
+    if (d.n > 0) {
+        k_scatter<<<nblk(d.n, 256), 256, 0, s>>>(d.cell, d.cell_start, d.cell_fill, d.perm, d.n);
+        k_sort_cells<<<nblk(ncell * 32, 256), 256, 0, s>>>(d.cell_start, d.perm, d.ids, d.perm2, ncell);
+    }
+    return cudaGetLastError();
+}
+
+// Swap the state buffers after a reorder pass.
+void swap_state(DevState &d)
+{
+    double *t;
+    t = d.r; d.r = d.r2; d.r2 = t;
+    t = d.v; d.v = d.v2; d.v2 = t;
+    t = d.q; d.q = d.q2; d.q2 = t;
+    t = d.j; d.j = d.j2; d.j2 = t;
+    int *ti = d.ids; d.ids = d.ids2; d.ids2 = ti;
+}
+
 // Scan of the histogram, scatter, in-cell sort, reorder + pack, then swap
 // the state buffers.  Expects cell[] and cell_count[] of the current order.
 cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaStream_t s)
 {
-    int nb = scan_blocks(g.ncell);
-    k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(d.cell_count, g.ncell, d.scan_tmp);
-    k_scan_top<<<1, SCAN_THREADS, 0, s>>>(d.scan_tmp, nb);
-    k_scan_down<<<nb, SCAN_THREADS, 0, s>>>(d.cell_count, g.ncell, d.scan_tmp, d.cell_start);
-    cudaError_t e = cudaMemsetAsync(d.cell_fill, 0, sizeof(int) * g.ncell, s);
+    cudaError_t e = launch_sort(g.ncell, d, s);
     if (e != cudaSuccess) return e;
-    if (d.n > 0) {
-        k_scatter<<<nblk(d.n, 256), 256, 0, s>>>(d.cell, d.cell_start, d.cell_fill, d.perm, d.n);
-        k_sort_cells<<<nblk(g.ncell * 32, 256), 256, 0, s>>>(d.cell_start, d.perm, d.ids, d.perm2, g.ncell);
-        k_reorder_pack<<<nblk(d.n, 256), 256, 0, s>>>(g, m, d);
-    }
+    if (d.n > 0) k_reorder_pack<<<nblk(d.n, 256), 256, 0, s>>>(g, m, d);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     double *t;

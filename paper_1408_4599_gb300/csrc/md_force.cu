@@ -17,148 +17,11 @@
 //   * full shell: each ordered pair from both sides, plain FP64 stores of
 //     the per-molecule totals, bitwise deterministic;
 //   * no FP64 arithmetic per pair: GB300's FP64 rate is ~1/70 of FP32.
-#include "md_pair.cuh"
+#include "md_forceop.cuh"
 
 using namespace mdk;
 
 namespace {
-
-struct ForceArgs {
-    Grid g;
-    DevModel m;
-    const int *cell_start;
-    const float4 *com;
-    const float4 *geo;
-    const double *r;
-    double *F, *tau;  // outputs (FP64, storage order)
-    float *acc;       // half shell: 6 x n FP32 accumulators (SoA)
-    long long n;
-    double *partials;
-    int *flags;
-};
-
-template <bool HALF>
-struct ForceExtra {
-    float jacc[HALF ? 6 : 1][JCAP];  // Newton-3 reactions: F (3), tau (3)
-    float ipart[32][6];              // i totals of the pass: F (3), tau (3)
-};
-
-template <class SIG, bool HALF>
-struct ForceOp {
-    static constexpr int IMAX = 32;
-    using Tile = WarpTile<ForceExtra<HALF>>;
-    const DevModel &m;
-    const ForceArgs &A;
-    int K;
-    int ig;
-    float pF0, pF1, pF2, pT0, pT1, pT2;
-    float cU, cW, cX, cY, cZ;                      // pass sums of energy and virial (FP32)
-    float sU, kU, sW, kW, sX, kX, sY, kY, sZ, kZ;  // compensated lane totals
-    int nmol, nexam;
-    Tile *T;
-
-    __device__ ForceOp(const DevModel &m_, const ForceArgs &A_, int K_, Tile *T_) : m(m_), A(A_), K(K_), T(T_)
-    {
-        sU = kU = sW = kW = sX = kX = sY = kY = sZ = kZ = 0.f;
-        nmol = nexam = 0;
-    }
-    __device__ void pass_begin(int ig_, int ni, int lane)
-    {
-        ig = ig_;
-        for (int t = lane; t < ni * 6; t += 32) (&T->x.ipart[0][0])[t] = 0.f;
-        cU = cW = cX = cY = cZ = 0.f;
-    }
-    __device__ void seg_begin(Tile &TT, int nj, int lane)
-    {
-        if (HALF)
-            for (int t = lane; t < nj; t += 32)
-#pragma unroll
-                for (int q = 0; q < 6; q++) TT.x.jacc[q][t] = 0.f;
-    }
-    __device__ void i_begin(const IMol<SIG> &, int) { pF0 = pF1 = pF2 = pT0 = pT1 = pT2 = 0.f; }
-    __device__ void count_examined(int n) { nexam += n; }
-    __device__ void pair(Tile &TT, const IMol<SIG> &I, int k, float X0, float X1, float X2, int js, int)
-    {
-        float Fp[3], tp[3], tq[3], Up;
-        mol_pair<SIG, HALF>(m, X0, X1, X2, I, A.geo + (long long)js * K, Fp, tp, tq, Up);
-        pF0 += Fp[0];
-        pF1 += Fp[1];
-        pF2 += Fp[2];
-        pT0 += tp[0];
-        pT1 += tp[1];
-        pT2 += tp[2];
-        cU += Up;
-        cW += X0 * Fp[0] + X1 * Fp[1] + X2 * Fp[2];
-        cX += X0 * Fp[0];
-        cY += X1 * Fp[1];
-        cZ += X2 * Fp[2];
-        nmol++;
-        if (HALF) {
-            TT.x.jacc[0][k] -= Fp[0];
-            TT.x.jacc[1][k] -= Fp[1];
-            TT.x.jacc[2][k] -= Fp[2];
-            TT.x.jacc[3][k] += tq[0];
-            TT.x.jacc[4][k] += tq[1];
-            TT.x.jacc[5][k] += tq[2];
-        }
-    }
-    __device__ void i_end(const IMol<SIG> &, int il, int lane)
-    {
-        for (int msk = 16; msk > 0; msk >>= 1) {
-            pF0 += __shfl_xor_sync(FULLMASK, pF0, msk);
-            pF1 += __shfl_xor_sync(FULLMASK, pF1, msk);
-            pF2 += __shfl_xor_sync(FULLMASK, pF2, msk);
-            pT0 += __shfl_xor_sync(FULLMASK, pT0, msk);
-            pT1 += __shfl_xor_sync(FULLMASK, pT1, msk);
-            pT2 += __shfl_xor_sync(FULLMASK, pT2, msk);
-        }
-        if (lane == 0) {
-            float *ip = T->x.ipart[il - ig];
-            ip[0] += pF0;
-            ip[1] += pF1;
-            ip[2] += pF2;
-            ip[3] += pT0;
-            ip[4] += pT1;
-            ip[5] += pT2;
-        }
-    }
-    __device__ void seg_end(Tile &TT, int nj, int lane)
-    {
-        if (HALF)
-            for (int t = lane; t < nj; t += 32) {
-                const int js = __float_as_int(TT.jc[t].w);
-#pragma unroll
-                for (int q = 0; q < 6; q++) atomicAdd(A.acc + (long long)q * A.n + js, TT.x.jacc[q][t]);
-            }
-    }
-    __device__ void pass_end(int s0, int ig_, int ni, int lane)
-    {
-        for (int t = lane; t < ni; t += 32) {
-            const int si = s0 + ig_ + t;
-            const float *ip = T->x.ipart[t];
-            if (HALF) {
-#pragma unroll
-                for (int q = 0; q < 6; q++) atomicAdd(A.acc + (long long)q * A.n + si, ip[q]);
-            } else {
-                double *Fo = A.F + 3LL * si, *To = A.tau + 3LL * si;
-                Fo[0] = ip[0];
-                Fo[1] = ip[1];
-                Fo[2] = ip[2];
-                To[0] = ip[3];
-                To[1] = ip[4];
-                To[2] = ip[5];
-                if (!(isfinite(ip[0]) && isfinite(ip[1]) && isfinite(ip[2]) && isfinite(ip[3]) && isfinite(ip[4]) &&
-                      isfinite(ip[5])))
-                    atomicExch(&A.flags[FLAG_NONFINITE], 1);
-            }
-        }
-        kahan_add(sU, kU, cU);
-        kahan_add(sW, kW, cW);
-        kahan_add(sX, kX, cX);
-        kahan_add(sY, kY, cY);
-        kahan_add(sZ, kZ, cZ);
-    }
-};
 
 template <class SIG, bool HALF>
 __global__ void __launch_bounds__(MD_WARPS * 32) k_force(const __grid_constant__ ForceArgs A)
@@ -276,6 +139,7 @@ cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half
     A.n = d.n;
     A.partials = d.partials;
     A.flags = d.flags;
+    A.to_acc = 0;
     // the grid may be smaller than the partials buffer: unused slots read as 0
     cudaError_t e = cudaMemsetAsync(d.partials, 0, sizeof(double) * P_COUNT * n_blocks, s);
     if (e != cudaSuccess) return e;
@@ -285,6 +149,12 @@ cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half
     }
     e = dispatch_sig(m, LaunchForce{A, half_shell, n_blocks, s});
     if (e != cudaSuccess || !half_shell || d.n == 0) return e;
+    return launch_force_finalize(d, s);
+}
+
+cudaError_t launch_force_finalize(DevState &d, cudaStream_t s)
+{
+    if (d.n == 0) return cudaSuccess;
     k_force_finalize<<<(unsigned)((d.n + 255) / 256), 256, 0, s>>>(d.facc, d.n, d.F, d.tau, d.flags);
     return cudaGetLastError();
 }

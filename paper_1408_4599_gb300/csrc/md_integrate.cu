@@ -72,8 +72,9 @@ __device__ __forceinline__ void quat_rate_f(const float q[4], const float w[3], 
 // half-step quaternion and its renormalisation) is formed in FP32 from the
 // rounded state, so its relative error (~1e-7) enters q only through the
 // dt-scaled update.  The final renormalisation of q uses the series
-// (1 + e)^(-1/2) = 1 - e/2 + 3e^2/8 - 5e^3/16 with e = |q|^2 - 1 (|e| ~ 1e-6),
-// exact to FP64 rounding.
+// (1 + e)^(-1/2) = 1 - e/2 + 3e^2/8 - 5e^3/16 with e = |q|^2 - 1 where it
+// is exact to FP64 rounding (|e| < 1e-4, the usual case), 1/sqrt(1 + e)
+// otherwise.
 __global__ void k_integrate(Grid g, DevModel m, DevState d, double dt)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -120,10 +121,11 @@ __global__ void k_integrate(Grid g, DevModel m, DevState d, double dt)
         quat_rate_f(qh, w, qd);
         for (int k = 0; k < 4; k++) q[k] += dt * (double)qd[k];  // Eq. 5: q(t + dt)
         const double e = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3] - 1.0;
-        const double inv = 1.0 + e * (-0.5 + e * (0.375 - 0.3125 * e));
+        // (1 + e)^(-1/2): the cubic series is exact to FP64 rounding for |e| < 1e-4
+        const double inv = fabs(e) < 1e-4 ? 1.0 + e * (-0.5 + e * (0.375 - 0.3125 * e)) : 1.0 / sqrt(1.0 + e);
         for (int k = 0; k < 4; k++) d.q[4 * s + k] = q[k] * inv;
         for (int k = 0; k < 3; k++) d.j[3 * s + k] = j[k];
-        bad |= !isfinite(q[0]) || fabs(e) > 0.01;
+        bad |= !isfinite(e);
     }
     if (bad) atomicExch(&d.flags[FLAG_NONFINITE], 1);
     const int c = (cc[2] * g.nc[1] + cc[1]) * g.nc[0] + cc[0];

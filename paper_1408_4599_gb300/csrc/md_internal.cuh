@@ -75,6 +75,16 @@ struct DevState {
     float *facc;                    // 6 x n FP32 force/torque accumulators (half shell)
 };
 
+// Compiled model of a system (used by the batched replicas, which compile
+// the model once through md_create).
+struct md_system;
+struct ModelInfo {
+    DevModel m;
+    Grid g;
+    double lrc_u_coef, lrc_w_coef, rf_self_per_mol;
+};
+void model_info(const md_system *s, ModelInfo *out);
+
 // Partial-sum layout of the force kernel (per block).
 enum { P_U = 0, P_W, P_WXX, P_WYY, P_WZZ, P_NMOL, P_NSITE, P_NEXAM, P_COUNT };
 
@@ -84,6 +94,8 @@ enum { FLAG_NONFINITE = 0, FLAG_OVERFLOW = 1, FLAG_TIMEOUT = 2 };
 // (all return cudaGetLastError() of the launch)
 cudaError_t launch_cellid(const Grid &g, DevState &d, cudaStream_t s);
 cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaStream_t s);
+cudaError_t launch_sort(long long ncell, DevState &d, cudaStream_t s);
+void swap_state(DevState &d);
 cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half_shell, int n_blocks,
                          cudaStream_t s);
 cudaError_t launch_integrate(const Grid &g, const DevModel &m, DevState &d, double dt, cudaStream_t s);
@@ -93,6 +105,7 @@ cudaError_t launch_scatter_out(const DevState &d, const double *src, int width, 
 cudaError_t launch_gather_in(DevState &d, const double *src, int width, double *dst, cudaStream_t s);
 cudaError_t launch_prepare_input(const Grid &g, DevState &d, cudaStream_t s);
 int force_blocks_default();
+cudaError_t launch_force_finalize(DevState &d, cudaStream_t s);
 int adjoint_nacc(const DevModel &m);
 cudaError_t launch_adjoint(const Grid &g, const DevModel &m, const DevState &d, int half_shell, int n_blocks,
                            double *partials, int nacc, cudaStream_t s);

@@ -67,7 +67,9 @@ _lib = None
 EXPORTS = ("md_create", "md_set_molecules", "md_compute_forces", "md_step", "md_energy_virial",
            "md_get_molecules", "md_get_forces", "md_n_molecules", "md_sync", "md_profile", "md_kernel_times_get",
            "md_destroy", "md_status_str", "md_last_error", "md_n_params", "md_get_params", "md_set_params",
-           "md_param_grad")
+           "md_param_grad", "md_batch_create", "md_batch_set_molecules", "md_batch_compute_forces", "md_batch_step",
+           "md_batch_energy_virial", "md_batch_get_molecules", "md_batch_get_forces", "md_batch_tune",
+           "md_batch_destroy", "md_batch_last_error", "md_kinetic_noalloc")
 
 
 def lib():
@@ -96,6 +98,22 @@ def lib():
         L.md_get_params.argtypes = [vp, dp]
         L.md_set_params.argtypes = [vp, dp, i32]
         L.md_param_grad.argtypes = [vp, i32, i64, vp, vp, i32, dp, dp, dp, vp]
+        L.md_batch_create.argtypes = [i32, dp, C.c_double, C.POINTER(md_site_types), C.POINTER(md_options),
+                                      C.POINTER(vp)]
+        L.md_batch_set_molecules.argtypes = [vp, C.POINTER(i64), vp, vp, vp, vp, i32, vp]
+        L.md_batch_compute_forces.argtypes = [vp, vp]
+        L.md_batch_step.argtypes = [vp, i32, C.c_double, i32, vp]
+        L.md_batch_energy_virial.argtypes = [vp, C.POINTER(md_observables), vp]
+        L.md_batch_get_molecules.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+        L.md_batch_get_forces.argtypes = [vp, vp, vp, i32, vp]
+        L.md_batch_tune.argtypes = [vp, vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_float)]
+        L.md_batch_destroy.argtypes = [vp]
+        L.md_batch_destroy.restype = None
+        L.md_batch_last_error.argtypes = [vp]
+        L.md_batch_last_error.restype = C.c_char_p
+        for name in ("md_batch_create", "md_batch_set_molecules", "md_batch_compute_forces", "md_batch_step",
+                     "md_batch_energy_virial", "md_batch_get_molecules", "md_batch_get_forces", "md_batch_tune"):
+            getattr(L, name).restype = C.c_int
         L.md_kinetic_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, C.c_double, dp, C.c_double, vp, vp]
         L.md_kinetic_noalloc.restype = C.c_int
         L.md_destroy.argtypes = [vp]
@@ -365,6 +383,84 @@ class System:
     def close(self):
         if self.h:
             md_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _bcheck(code, handle):
+    if code != MD_OK:
+        raise MDError(code, lib().md_batch_last_error(handle).decode() if handle else lib().md_status_str(code).decode())
+
+
+class Batch:
+    """Owning wrapper of an md_batch: replicas of one model (cfgs share the
+    model dict, the cut-off and the options)."""
+
+    def __init__(self, cfgs, half_shell=1):
+        c0 = cfgs[0]
+        self.cfgs = cfgs
+        self._model = Model(c0["model"])
+        boxes = np.ascontiguousarray(np.array([c["box"] for c in cfgs], dtype=np.float64))
+        o = md_options(float(c0.get("eps_rf", math.inf)), int(c0.get("lj_shift", 0)), int(c0.get("lj_lrc", 0)), 0,
+                       int(half_shell))
+        h = C.c_void_p()
+        _check(lib().md_batch_create(len(cfgs), boxes.ctypes.data_as(dp), float(c0["rc"]), C.byref(self._model.types),
+                                     C.byref(o), C.byref(h)))
+        self.h = h
+        self.n_per = np.array([c["r"].shape[0] for c in cfgs], dtype=np.int64)
+
+    def set(self, r=None, q=None, v=None, j=None, stream=None):
+        """Concatenated state; by default the cfgs' own r, q, v, j."""
+        if r is None:
+            r = np.concatenate([c["r"] for c in self.cfgs])
+            q = np.concatenate([c["q"] for c in self.cfgs])
+            v = np.concatenate([c["v"] for c in self.cfgs])
+            j = np.concatenate([c["j"] for c in self.cfgs])
+        ptrs = [_ptr(a) for a in (r, v, q, j)]
+        dev = ptrs[0][1]
+        n = self.n_per.ctypes.data_as(C.POINTER(C.c_int64))
+        _bcheck(lib().md_batch_set_molecules(self.h, n, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], dev,
+                                             _stream_ptr(stream)), self.h)
+        return self
+
+    def compute_forces(self, stream=None):
+        _bcheck(lib().md_batch_compute_forces(self.h, _stream_ptr(stream)), self.h)
+
+    def step(self, n_steps, dt, use_graph=True, stream=None):
+        _bcheck(lib().md_batch_step(self.h, int(n_steps), float(dt), int(bool(use_graph)), _stream_ptr(stream)),
+                self.h)
+
+    def observables(self, stream=None):
+        out = (md_observables * len(self.cfgs))()
+        _bcheck(lib().md_batch_energy_virial(self.h, out, _stream_ptr(stream)), self.h)
+        return [o.as_dict() for o in out]
+
+    def molecules(self, stream=None):
+        n = int(self.n_per.sum())
+        r, v, q, j = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 4)), np.zeros((n, 3))
+        ptrs = [_ptr(a) for a in (r, v, q, j)]
+        _bcheck(lib().md_batch_get_molecules(self.h, *[p[0] for p in ptrs], 0, _stream_ptr(stream)), self.h)
+        return r, v, q, j
+
+    def forces(self, stream=None):
+        n = int(self.n_per.sum())
+        F, tau = np.zeros((n, 3)), np.zeros((n, 3))
+        _bcheck(lib().md_batch_get_forces(self.h, _ptr(F)[0], _ptr(tau)[0], 0, _stream_ptr(stream)), self.h)
+        return F, tau
+
+    def tune(self, stream=None):
+        bc, bg, bm = C.c_int32(), C.c_int32(), C.c_float()
+        _bcheck(lib().md_batch_tune(self.h, _stream_ptr(stream), C.byref(bc), C.byref(bg), C.byref(bm)), self.h)
+        return {"chunk": bc.value, "grid_pct": bg.value, "force_ms": bm.value}
+
+    def close(self):
+        if self.h:
+            lib().md_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,0 +1,133 @@
+"""Batched replicas (md_batch_*): one launch per kernel over many uneven
+systems must give every replica the same result as evaluating it alone,
+and the FP64 oracle's result within the force-parity tolerances."""
+import math
+
+import numpy as np
+import pytest
+
+import mdgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1408_4599_gb300 import md  # noqa: E402
+from test_gpu_parity import check_parity, rel_err  # noqa: E402
+
+
+def _replicas(n_rep=9, n_min=300, n_max=3000, seed_k=3):
+    specs = mdgen.replica_specs(n_rep, n_min, n_max, seed_k=seed_k)
+    cfgs = []
+    for k, (n, rho, T) in enumerate(specs):
+        rho = max(rho, 0.1)
+        if (n / rho) ** (1 / 3) < 6.0:  # box >= 2 rc
+            rho = n / 6.0 ** 3
+        cfgs.append(mdgen.config_replica(k, n, rho, T))
+    return cfgs
+
+
+def _split(a, cfgs):
+    out, s = [], 0
+    for c in cfgs:
+        n = c["r"].shape[0]
+        out.append(a[s:s + n])
+        s += n
+    return out
+
+
+@pytest.mark.parametrize("half", [1, 0])
+def test_batch_forces_match_oracle_per_replica(half):
+    cfgs = _replicas()
+    assert any(min(int(L // 3.0) for L in c["box"]) < 3 for c in cfgs)  # includes small boxes
+    b = md.Batch(cfgs, half_shell=half).set()
+    b.compute_forces()
+    F, tau = b.forces()
+    obs = b.observables()
+    b.close()
+    for c, Fk, tk, ok in zip(cfgs, _split(F, cfgs), _split(tau, cfgs), obs):
+        s = oracle.setup_from_config(c)
+        Fo, to, oo = oracle.forces(c["model"], s, c["r"], c["q"], use_cells=True)
+        ncs = [int(math.floor(L / (c["rc"] * (1 + 1e-9)))) for L in c["box"]]
+        check_parity(f"batch/{c['name']}/half{half}", c, Fk, tk, ok, Fo, to, oo, exact_examined=min(ncs) >= 3)
+        assert ok["n_molecules"] == c["r"].shape[0]
+
+
+def test_batch_equals_single_systems():
+    """Full stencil everywhere: the batched kernels and the single-system
+    kernels do the same arithmetic in the same order per molecule."""
+    cfgs = _replicas(n_rep=6, seed_k=5)
+    b = md.Batch(cfgs, half_shell=0).set()
+    b.step(6, 0.001, use_graph=False)
+    rb, vb, qb, jb = b.molecules()
+    obs_b = b.observables()
+    b.close()
+    for c, r, v, q, o_b in zip(cfgs, _split(rb, cfgs), _split(vb, cfgs), _split(qb, cfgs), obs_b):
+        s = md.System(c, deterministic=1)
+        s.set(c["r"], c["q"], c["v"], c["j"])
+        s.step(6, 0.001)
+        r1, v1, q1, j1 = s.molecules()
+        o1 = s.observables()
+        s.close()
+        L = np.array(c["box"])
+        dr = r - r1
+        dr -= L * np.rint(dr / L)
+        assert np.abs(dr).max() < 1e-11 and np.abs(v - v1).max() < 1e-9
+        assert np.abs(q - q1).max() < 1e-11
+        assert o_b["n_mol_pairs"] == o1["n_mol_pairs"]
+        assert o_b["U_pot"] == pytest.approx(o1["U_pot"], rel=1e-9, abs=1e-9)
+        assert o_b["K_trans"] == pytest.approx(o1["K_trans"], rel=1e-12)
+        assert o_b["K_rot"] == pytest.approx(o1["K_rot"], rel=1e-12)
+        assert o_b["U_lrc"] == pytest.approx(o1["U_lrc"], rel=1e-12)
+
+
+def test_graph_replay_equals_eager_steps():
+    cfgs = _replicas(n_rep=5, seed_k=7)
+    res = []
+    for use_graph in (False, True):
+        b = md.Batch(cfgs, half_shell=0).set()
+        b.step(5, 0.001, use_graph=use_graph)   # 2 graph replays + 1 eager step
+        b.step(4, 0.001, use_graph=use_graph)   # other buffer parity
+        res.append(b.molecules())
+        o = b.observables()
+        assert all(x["step"] == 9 for x in o)
+        b.close()
+    for a, c in zip(res[0], res[1]):
+        assert np.array_equal(a, c)
+
+
+def test_tuner_and_nve_energy():
+    cfgs = _replicas(n_rep=6, seed_k=9)
+    for c in cfgs:
+        c["v"] *= 0.3
+        c["j"] *= 0.3
+    b = md.Batch(cfgs, half_shell=1).set()
+    t = b.tune()
+    assert t["chunk"] in (1, 2, 4, 8, 16) and t["grid_pct"] in (50, 100) and t["force_ms"] > 0
+    b.step(2, 0.0005)
+    e0 = [o["U_pot"] + o["K_trans"] + o["K_rot"] for o in b.observables()]
+    b.step(20, 0.0005)
+    e1 = [o["U_pot"] + o["K_trans"] + o["K_rot"] for o in b.observables()]
+    b.close()
+    for a, c, cfg in zip(e0, e1, cfgs):
+        assert np.isfinite(c)
+        # no blow-up: lattice starts with overlapping sites carry large energies;
+        # the centre-of-mass cut-off also lets E jump when pairs cross r_c
+        assert abs(c - a) < 0.01 * max(abs(a), cfg["r"].shape[0])
+
+
+def test_batch_argument_errors():
+    cfgs = _replicas(n_rep=2)
+    boxes = np.array([c["box"] for c in cfgs], dtype=np.float64)
+    boxes[1, 2] = 5.0  # < 2 rc
+    L = md.lib()
+    M = md.Model(cfgs[0]["model"])
+    h = md.C.c_void_p()
+    o = md.md_options(math.inf, 0, 1, 0, 1)
+    assert L.md_batch_create(2, boxes.ctypes.data_as(md.dp), 3.0, md.C.byref(M.types), md.C.byref(o),
+                             md.C.byref(h)) == -2
+    b = md.Batch(cfgs)
+    with pytest.raises(md.MDError) as e:
+        b.compute_forces()
+    assert e.value.code == -3
+    b.close()
