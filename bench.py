@@ -165,6 +165,10 @@ def main():
     ap.add_argument("--shell", default="half", choices=["half", "full"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="2cljq", choices=["2cljq", "batch", "adjoint"],
+                    help="2cljq: the headline step; batch: 512 uneven replicas; adjoint: parameter gradients")
+    ap.add_argument("--replicas", type=int, default=512)
+    ap.add_argument("--configs", type=int, default=4, help="adjoint workload: configurations per ensemble")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -180,6 +184,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
+    if args.workload == "batch":
+        return run_batch(args, md, torch, dev, rank)
+    if args.workload == "adjoint":
+        return run_adjoint(args, md, torch, dev, rank)
     cfg = mdgen.config_2cljq(seed_k=rank)
     half = args.shell == "half"
     sysm = md.System(cfg, deterministic=0 if half else 1, half_shell=1 if half else 0)
@@ -297,6 +305,118 @@ def e2e_run(args, cfg, md, torch, dev):
     return {"value": pairs / dt, "unit": UNIT, "h2d_bytes_per_step": n * 13 * 8,
             "d2h_bytes_per_step": n * 13 * 8 + 160, "ms_per_step": 1e3 * dt / args.steps,
             "note": "host->device state, md_step (incl. the stale-force evaluation), device->host state"}
+
+
+def run_batch(args, md, torch, dev, rank):
+    """512 independent 2CLJQ + dipole replicas (N log-uniform in [500,
+    20000], rho ~ U(0.05, 0.75), T ~ U(0.7, 1.3), rc = 3, eps_RF = inf),
+    advanced with md_batch_step (graph-replayed pairs of steps) versus the
+    same replicas as separate md_system handles stepped one after another."""
+    specs = mdgen.replica_specs(args.replicas)
+    # every box at least 2 r_c = 6 (N >= 500 and rho <= 0.75 already give L > 8.7)
+    cfgs = [mdgen.config_replica(k, n, min(rho, n / 216.0), T) for k, (n, rho, T) in enumerate(specs)]
+    dt = 0.001
+    stream = torch.cuda.current_stream(dev)
+    b = md.Batch(cfgs, half_shell=1).set()
+    tune = b.tune()
+    b.step(args.warmup, dt, use_graph=True)
+    o0 = b.observables()
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.steps, dt, use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    o1 = b.observables()
+    b.close()
+    pairs_step = 0.5 * (sum(o["n_site_pairs"] for o in o0) + sum(o["n_site_pairs"] for o in o1))
+    n_tot = sum(c["r"].shape[0] for c in cfgs)
+    # sequential reference: one md_system per replica, one md_step launch sequence each
+    systems = [md.System(c, deterministic=0, half_shell=1).set(c["r"], c["q"], c["v"], c["j"]) for c in cfgs]
+    for s in systems:
+        s.step(args.warmup, dt)
+    seq_steps = max(1, min(args.steps, 20))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(seq_steps):
+        for s in systems:
+            s.step(1, dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1e3
+    for s in systems:
+        s.close()
+    value = pairs_step * args.steps / t_batch
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_batch / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 site math, f64 accumulation/state", "data": "synthetic (seeded)",
+            "config": {"workload": f"{len(cfgs)} 2CLJQ+dipole replicas, N log-uniform [500,20000] (sum {n_tot}), "
+                                   "rc=3, eps_RF=inf, one batched md step (CUDA graph)",
+                       "l2": "working set > L2 (not flushed)"},
+            "molecule_updates_per_s": n_tot * args.steps / t_batch,
+            "sequential": {"value": pairs_step * seq_steps / t_seq, "ms_per_step": 1e3 * t_seq / seq_steps,
+                           "note": f"{len(cfgs)} separate md_system handles, md_step(1) each per step"},
+            "speedup_vs_sequential": (t_seq / seq_steps) / (t_batch / args.steps),
+            "tuned": tune, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_adjoint(args, md, torch, dev, rank):
+    """Force-field parameter gradients of the 4-site polar model (N = 50,000,
+    rho = 0.5, rc = 3): md_param_grad over an ensemble of configurations,
+    beside the plain force kernel on the same configurations."""
+    from paper_1408_4599_gb300.autograd import ensemble_uw
+    cfgs = [mdgen.config_4site(cfg=c) for c in range(args.configs)]
+    r_all = torch.from_numpy(np.stack([c["r"] for c in cfgs])).to(dev)
+    q_all = torch.from_numpy(np.stack([c["q"] for c in cfgs])).to(dev)
+    s = md.System(cfgs[0], deterministic=0, half_shell=1)
+    theta = torch.tensor(s.params(), dtype=torch.float64, requires_grad=True)
+    for _ in range(2):
+        s.param_grad(r_all, q_all)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = max(1, args.steps // 4)
+    for _ in range(reps):
+        dU, dW, U, W = s.param_grad(r_all, q_all)
+    torch.cuda.synchronize()
+    t_adj = (time.perf_counter() - t0) / reps
+    md.md_profile(s.h, True)
+    md.md_kernel_times_get(s.h)
+    pairs = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in range(len(cfgs)):
+        s.set(r_all[c], q_all[c])
+        s.compute_forces()
+        pairs += s.observables()["n_site_pairs"]
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    kt = md.md_kernel_times_get(s.h)
+    md.md_profile(s.h, True)
+    md.md_kernel_times_get(s.h)
+    s.param_grad(r_all, q_all)
+    kt_adj = md.md_kernel_times_get(s.h)
+    md.md_profile(s.h, False)
+    out = ensemble_uw(theta, s, r_all, q_all)
+    (out[0] + out[1]).backward()
+    s.close()
+    line = {"metric": METRIC, "value": pairs / t_adj, "unit": UNIT, "n_gpus": 1, "steps": reps, "warmup": 2,
+            "ms_per_step": 1e3 * t_adj, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 pair terms, f64 block sums", "data": "synthetic (seeded 4-site polar model)",
+            "config": {"workload": f"d<U>/dtheta and d<W>/dtheta, 4-site model N=50000 rho=0.5 rc=3, "
+                                   f"{len(cfgs)} configurations, P={len(dU)}"},
+            "adjoint_kernel_ms_per_config": kt_adj["adjoint"]["ms"] / max(kt_adj["adjoint"]["launches"], 1),
+            "forward_force_kernel_ms_per_config": kt["force"]["ms"] / max(kt["force"]["launches"], 1),
+            "forward_ms_per_ensemble": 1e3 * t_fwd, "adjoint_ms_per_ensemble": 1e3 * t_adj,
+            "dU": dU.tolist(), "dW": dW.tolist(), "U_mean": U, "W_mean": W,
+            "autograd_grad": theta.grad.tolist()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -1,44 +1,46 @@
 /*
  * md_flops.h -- algorithmic FP32 operation counts per unordered interacting
- * molecule pair, frozen from the expression trees of the site-site kernels
- * in paper_1408_4599_gb300/csrc/md_force.cu (mol_pair + elec_site).
+ * molecule pair, taken from the expression trees of the site-site code in
+ * paper_1408_4599_gb300/csrc/md_pair.cuh (mol_pair, elec_site, law) and the
+ * per-pair accumulation of csrc/md_forceop.cuh (ForceOp::pair).
  *
- * Counting rule: FMA = 2; add, sub, mul, compare/select = 1; rcp/rsqrt = 1
- * (the MUFU count is listed separately).  "Per unordered pair" means the
- * work that yields the pair energy, the pair virial, the force on both
- * molecules (equal and opposite) and the torque on both molecules, done
- * once -- i.e. the half-shell (Newton-3) kernel's count.  The full-shell
- * kernel executes the i-side part twice per pair; that repetition is not
- * counted as useful work.  The centre-of-mass distance test of an examined
- * candidate (12 FLOP) is overhead and is not counted either (§3: only ~16%
- * of the examined pairs interact).
+ * Counting rule: FMA = 2; add, sub, mul = 1; rcp / rsqrt = 1 (the MUFU
+ * count is listed separately); a negation folded into an operand and a
+ * product reused by common-subexpression elimination are not counted again.
+ * "Per unordered pair" means the work that yields the pair energy, the pair
+ * virial, the force on both molecules (equal and opposite) and the torque
+ * on both molecules, done once -- the half-shell (Newton-3) kernel's count.
+ * The full-shell kernel repeats the i-side part for the reversed pair; that
+ * repetition is not counted as useful work.  The centre-of-mass distance
+ * test of an examined candidate (MD_FLOPS_EXAMINED) is overhead and is not
+ * counted either (§3: only ~16% of the examined pairs interact).
  *
- * Building blocks (source expression trees):
- *   site vector x = X + d_a - d_b ............................ 6
- *   r^2 ...................................................... 5
- *   LJ: rcp 1, s2 1, s6 2, F/r 5, energy 5, force 3 ........... 17  (1 MUFU)
- *   accumulate the force on site a and on site b ............. 6
- *     => one LJ-LJ site pair ................................. 34
- *   QQ site pair: x 6, r^2 5, rsqrt 1, ir^2 1, xh 3,
- *     pa/pb/cab 15, u^2 u^3 2, law 44, U 1, radial coeff. 5,
- *     ua ub 2, force 18, e_a x e_b 9, torque on i 21,
- *     accumulate 6 ........................................... 139 (1 MUFU)
- *     + torque on j 21 ....................................... 160
- *   per molecule pair: total force 3 per site of j, energy 1,
- *     virial 6, virial diagonal 6; lever-arm torque of j
- *     9 per site of j.
+ * Building blocks:
+ *   lever arm X + d_a, once per site of i ..................... 3
+ *   LJ-LJ site pair: x = (X + d_a) - d_b 3, r^2 5, rcp 1, s^2 1,
+ *     s^6 2, F/r 5, energy 5, site force 3, sum into site a 3 . 28  (1 MUFU)
+ *   quadrupole-quadrupole site pair: x 3, r^2 5, rsqrt 1, unit
+ *     vector 3, p_a p_b cos_ab 15, law 38, strength 6, energy 1,
+ *     radial coefficient 5, axial coefficients 2, force 18,
+ *     e_a x e_b 9, orientation torque on i 21, sum into a 3 ... 130 (1 MUFU)
+ *   per molecule pair: total force 3 per site of i, lever-arm
+ *     torque 12 per site of i, torque on j from the angular-
+ *     momentum balance tau_j = -tau_i - X x F 12, accumulation
+ *     of F and tau on i 6, energy 1, virial (trace and
+ *     diagonal) 9, Newton-3 reaction on j 6.
  */
 #ifndef MD_FLOPS_H
 #define MD_FLOPS_H
 
 /* single LJ site at the centre of mass (LJ / LJTS fluids):
- * r^2 5 + LJ 17 + accumulate 3 + energy 1 + virial 6 + diagonal 6 = 38 */
-#define MD_FLOPS_PAIR_LJ1 38
+ * r^2 5 + rcp 1 + s^2 1 + s^6 2 + F/r 5 + energy 4 + force 3
+ * + accumulate F on i 3 + energy 1 + virial 9 + reaction on j 3 = 37 */
+#define MD_FLOPS_PAIR_LJ1 37
 #define MD_MUFU_PAIR_LJ1 1
 
 /* 2CLJQ: 2 LJ sites + 1 linear quadrupole at the centre of mass:
- * 4 x 34 + 160 + 3 x 3 + 13 + 3 x 9 = 345 */
-#define MD_FLOPS_PAIR_2CLJQ 345
+ * 3 x 3 + 4 x 28 + 130 + 3 x 3 + 3 x 12 + 12 + 6 + 1 + 9 + 6 = 330 */
+#define MD_FLOPS_PAIR_2CLJQ 330
 #define MD_MUFU_PAIR_2CLJQ 5
 
 /* distance test of one examined candidate (overhead, not counted above) */
