@@ -48,6 +48,7 @@ struct md_system {
     int n_force_blocks, n_kin_blocks;
     long long cap;               // allocated molecules
     bool has_mol, binned, forces_valid;
+    bool f_in_acc;               // the latest forces exist only in the FP32 accumulators (half shell)
     double dt_last, time;
     long long step;
     cudaStream_t last_stream;
@@ -518,6 +519,19 @@ md_status do_force(md_system *s, cudaStream_t st)
     TimeScope ts(s, st, 3);
     CK(launch_force(s->g, s->m, s->d, s->half_eff, s->n_force_blocks, st), "force kernel");
     s->forces_valid = true;
+    s->f_in_acc = s->half_eff != 0;
+    return MD_OK;
+}
+
+// FP64 F and tau for the callers that read them (observables, md_get_forces):
+// the integrator reads the FP32 accumulators directly, so the conversion
+// runs only when something outside the step needs it.
+md_status forces_to_f64(md_system *s, cudaStream_t st)
+{
+    if (!s->f_in_acc) return MD_OK;
+    TimeScope ts(s, st, 7);
+    CK(launch_force_finalize(s->d, st), "force finalize kernel");
+    s->f_in_acc = false;
     return MD_OK;
 }
 
@@ -583,6 +597,7 @@ md_status md_create(const double box[3], double cutoff, const md_site_types *typ
         g.nc[k] = nc < 1 ? 1 : nc;
         g.L[k] = box[k];
         g.ell[k] = box[k] / g.nc[k];
+        g.iell[k] = 1.0 / g.ell[k];
         g.ellf[k] = (float)g.ell[k];
         ncell *= g.nc[k];
     }
@@ -684,6 +699,7 @@ md_status md_set_molecules(md_system *s, int64_t n, const int32_t *comp_id, cons
     s->has_mol = true;
     s->binned = false;
     s->forces_valid = false;
+    s->f_in_acc = false;
     s->dt_last = 0.0;
     s->time = 0.0;
     s->step = 0;
@@ -738,7 +754,7 @@ md_status md_step(md_system *s, int32_t n_steps, double dt, double T_target, voi
     for (int k = 0; k < n_steps; k++) {
         {
             TimeScope ts(s, st, 0);
-            CK(launch_integrate(s->g, s->m, s->d, dt, st), "integrate kernel");
+            CK(launch_integrate(s->g, s->m, s->d, dt, s->f_in_acc ? 1 : 0, st), "integrate kernel");
         }
         md_status ms = do_rebuild(s, st, false);
         if (ms != MD_OK) return ms;
@@ -754,6 +770,8 @@ md_status md_step(md_system *s, int32_t n_steps, double dt, double T_target, voi
 md_status md_sync(md_system *s, void *cuda_stream)
 {
     if (!s) return MD_ERR_ARG;
+    md_status mf = forces_to_f64(s, (cudaStream_t)cuda_stream);  // also checks the latest forces for non-finite values
+    if (mf != MD_OK) return mf;
     CK(cudaStreamSynchronize((cudaStream_t)cuda_stream), "stream synchronize");
     if (s->profiling) drain_timings(s);
     return check_flags(s);
@@ -767,6 +785,8 @@ md_status md_energy_virial(md_system *s, md_observables *out)
         return MD_ERR_STATE;
     }
     cudaStream_t st = s->last_stream;
+    md_status mf = forces_to_f64(s, st);
+    if (mf != MD_OK) return mf;
     {
         TimeScope ts(s, st, 4);
         CK(launch_kinetic(s->m, s->d, 0.5 * s->dt_last, s->n_kin_blocks, st), "kinetic kernel");
@@ -844,6 +864,8 @@ md_status md_get_forces(md_system *s, double *F, double *tau, int32_t on_device,
         return MD_ERR_STATE;
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    md_status mf = forces_to_f64(s, st);
+    if (mf != MD_OK) return mf;
     DevState &d = s->d;
     const double *src[2] = {d.F, d.tau};
     double *dst[2] = {F, tau};

@@ -27,6 +27,7 @@
 
 #include "../../include/md.h"
 #include "md_forceop.cuh"
+#include "md_leapfrog.cuh"
 
 using namespace mdk;
 
@@ -37,6 +38,7 @@ struct RepGrid {
     float ellf[3];
     double L[3];
     double ell[3];
+    double iell[3];  // 1 / ell
     long long cell0, mol0;
 };
 
@@ -62,6 +64,7 @@ struct md_batch {
     double *rep_obs = nullptr;  // 8 per replica
     double *rep_kin = nullptr;  // 2 per replica
     bool has_mol = false, forces_valid = false;
+    bool f_in_acc = false;  // the latest forces exist only in the FP32 accumulators
     double dt_last = 0.0, time = 0.0;
     long long step = 0;
     int chunk = 2, grid_frac_pct = 100;
@@ -72,12 +75,6 @@ struct md_batch {
 };
 
 namespace {
-
-__device__ __forceinline__ int cell_axis_b(double x, double ell, int nc)
-{
-    int c = (int)floor(x / ell);
-    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
-}
 
 __global__ void k_prepare_b(const RepGrid *G, const int *rep, double *r, double *q, int *ids, long long n, int *flags)
 {
@@ -106,87 +103,24 @@ __global__ void k_cellid_b(const RepGrid *G, const int *rep, const double *r, in
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const RepGrid &g = G[rep[s]];
-    const int cx = cell_axis_b(r[3 * s], g.ell[0], g.nc[0]);
-    const int cy = cell_axis_b(r[3 * s + 1], g.ell[1], g.nc[1]);
-    const int cz = cell_axis_b(r[3 * s + 2], g.ell[2], g.nc[2]);
+    const int cx = cell_coord(r[3 * s], g.iell[0], g.nc[0]);
+    const int cy = cell_coord(r[3 * s + 1], g.iell[1], g.nc[1]);
+    const int cz = cell_coord(r[3 * s + 2], g.iell[2], g.nc[2]);
     const int c = (int)g.cell0 + (cz * g.nc[1] + cy) * g.nc[0] + cx;
     cell[s] = c;
     atomicAdd(&count[c], 1);
 }
 
-// Leapfrog of §3 (Eqs. 2-5) with the same precision split as the
-// single-system integrator; per-slot replica box for wrap and cell id.
-__device__ __forceinline__ void omega_b(const float q[4], const float j[3], const float Iinv[3], float w[3])
-{
-    const float qw = q[0], qx = q[1], qy = q[2], qz = q[3];
-    const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
-    const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
-    const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
-    w[0] = Iinv[0] * (R00 * j[0] + R10 * j[1] + R20 * j[2]);
-    w[1] = Iinv[1] * (R01 * j[0] + R11 * j[1] + R21 * j[2]);
-    w[2] = Iinv[2] * (R02 * j[0] + R12 * j[1] + R22 * j[2]);
-}
-
-__device__ __forceinline__ void qrate_b(const float q[4], const float w[3], float qd[4])
-{
-    qd[0] = 0.5f * (-q[1] * w[0] - q[2] * w[1] - q[3] * w[2]);
-    qd[1] = 0.5f * (q[0] * w[0] + q[2] * w[2] - q[3] * w[1]);
-    qd[2] = 0.5f * (q[0] * w[1] + q[3] * w[0] - q[1] * w[2]);
-    qd[3] = 0.5f * (q[0] * w[2] + q[1] * w[1] - q[2] * w[0]);
-}
-
-__global__ void k_integrate_b(const RepGrid *G, const int *rep, DevModel m, DevState d, double dt)
+// Leapfrog of §3 (Eqs. 2-5), the single-system step of md_leapfrog.cuh
+// with the slot's replica box; the forces come from the FP32 accumulators,
+// which every replica's force pass fills.
+__global__ void k_integrate_b(const RepGrid *G, const int *rep, DevModel m, DevState d, LeapArgs a)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= d.n) return;
     const RepGrid &g = G[rep[s]];
-    const double dtm = dt / m.mass;
     int cc[3];
-    bool bad = false;
-    for (int k = 0; k < 3; k++) {
-        const double v = d.v[3 * s + k] + dtm * d.F[3 * s + k];
-        double r = d.r[3 * s + k] + dt * v;
-        bad |= !isfinite(r);
-        if (r < 0.0) r += g.L[k];
-        else if (r >= g.L[k]) r -= g.L[k];
-        if (!(r >= 0.0 && r < g.L[k])) {
-            r -= g.L[k] * floor(r / g.L[k]);
-            if (r >= g.L[k]) r -= g.L[k];
-            if (r < 0.0) r = 0.0;
-        }
-        d.v[3 * s + k] = v;
-        d.r[3 * s + k] = r;
-        cc[k] = cell_axis_b(r, g.ell[k], g.nc[k]);
-    }
-    if (m.rot_dof > 0) {
-        double q[4] = {d.q[4 * s], d.q[4 * s + 1], d.q[4 * s + 2], d.q[4 * s + 3]};
-        double j[3] = {d.j[3 * s], d.j[3 * s + 1], d.j[3 * s + 2]};
-        const double t[3] = {d.tau[3 * s], d.tau[3 * s + 1], d.tau[3 * s + 2]};
-        const float Iinv[3] = {(float)m.Iinv[0], (float)m.Iinv[1], (float)m.Iinv[2]};
-        const float hdt = (float)(0.5 * dt);
-        float qf[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
-        float jt[3], w[3], qd[4], qh[4], jh[3];
-        for (int k = 0; k < 3; k++) jt[k] = (float)j[k] + hdt * (float)t[k];
-        omega_b(qf, jt, Iinv, w);
-        qrate_b(qf, w, qd);
-        for (int k = 0; k < 4; k++) qh[k] = qf[k] + hdt * qd[k];
-        const float nh = rsqrtf(qh[0] * qh[0] + qh[1] * qh[1] + qh[2] * qh[2] + qh[3] * qh[3]);
-        for (int k = 0; k < 4; k++) qh[k] *= nh;
-        for (int k = 0; k < 3; k++) {
-            j[k] += dt * t[k];
-            jh[k] = (float)j[k];
-        }
-        omega_b(qh, jh, Iinv, w);
-        qrate_b(qh, w, qd);
-        for (int k = 0; k < 4; k++) q[k] += dt * (double)qd[k];
-        const double e = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3] - 1.0;
-        // (1 + e)^(-1/2): the cubic series is exact to FP64 rounding for |e| < 1e-4
-        const double inv = fabs(e) < 1e-4 ? 1.0 + e * (-0.5 + e * (0.375 - 0.3125 * e)) : 1.0 / sqrt(1.0 + e);
-        for (int k = 0; k < 4; k++) d.q[4 * s + k] = q[k] * inv;
-        for (int k = 0; k < 3; k++) d.j[3 * s + k] = j[k];
-        bad |= !isfinite(e);
-    }
-    if (bad) atomicExch(&d.flags[FLAG_NONFINITE], 1);
+    if (leapfrog_one<true>(m, d, s, a, g.L, g.iell, g.nc, cc)) atomicExch(&d.flags[FLAG_NONFINITE], 1);
     const int c = (int)g.cell0 + (cc[2] * g.nc[1] + cc[1]) * g.nc[0] + cc[0];
     d.cell[s] = c;
     atomicAdd(&d.cell_count[c], 1);
@@ -456,8 +390,18 @@ md_status batch_force(md_batch *b, cudaStream_t st)
         BatchArgs B = batch_args(b, h == 1);
         BCK(dispatch_sig(b->m, LaunchBatchForce{B, h, b->grid_frac_pct, st}), "batched force kernel");
     }
-    BCK(launch_force_finalize(d, st), "force finalize");
     b->forces_valid = true;
+    b->f_in_acc = true;
+    return MD_OK;
+}
+
+// FP64 F and tau for the readers outside the step (the integrator reads the
+// FP32 accumulators).
+md_status batch_forces_to_f64(md_batch *b, cudaStream_t st)
+{
+    if (!b->f_in_acc) return MD_OK;
+    BCK(launch_force_finalize(b->d, st), "force finalize");
+    b->f_in_acc = false;
     return MD_OK;
 }
 
@@ -479,7 +423,7 @@ md_status batch_one_step(md_batch *b, double dt, cudaStream_t st)
 {
     DevState &d = b->d;
     BCK(cudaMemsetAsync(d.cell_count, 0, sizeof(int) * b->ncell, st), "zero counts");
-    if (d.n > 0) k_integrate_b<<<nb256(d.n), 256, 0, st>>>(b->dgrids, b->rep_of_slot, b->m, d, dt);
+    if (d.n > 0) k_integrate_b<<<nb256(d.n), 256, 0, st>>>(b->dgrids, b->rep_of_slot, b->m, d, leap_args(b->m, dt));
     BCK(cudaGetLastError(), "integrate kernel");
     md_status ms = batch_rebuild(b, st, false);
     if (ms != MD_OK) return ms;
@@ -560,6 +504,7 @@ md_status md_batch_create(int32_t n_sys, const double *boxes, double cutoff, con
             g.nc[a] = nc < 1 ? 1 : nc;
             g.L[a] = boxes[3 * k + a];
             g.ell[a] = g.L[a] / g.nc[a];
+            g.iell[a] = 1.0 / g.ell[a];
             g.ellf[a] = (float)g.ell[a];
             all3 = all3 && g.nc[a] >= 3;
         }
@@ -723,6 +668,7 @@ md_status md_batch_set_molecules(md_batch *b, const int64_t *n_per_sys, const do
     if (ms != MD_OK) return ms;
     b->has_mol = true;
     b->forces_valid = false;
+    b->f_in_acc = false;
     b->dt_last = b->time = 0.0;
     b->step = 0;
     b->parity = 0;
@@ -792,6 +738,8 @@ md_status md_batch_step(md_batch *b, int32_t n_steps, double dt, int32_t use_gra
     b->time += n_steps * dt;
     b->dt_last = dt;
     b->forces_valid = true;
+    // a replayed graph runs no host code: the flag is set here, not by batch_force
+    b->f_in_acc = true;
     return MD_OK;
 }
 
@@ -804,6 +752,8 @@ md_status md_batch_energy_virial(md_batch *b, md_observables *out, void *cuda_st
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     DevState &d = b->d;
+    md_status mf = batch_forces_to_f64(b, st);
+    if (mf != MD_OK) return mf;
     k_rep_reduce<<<b->n_sys, 256, 0, st>>>(b->dgrids, b->n_sys, b->ncell, b->cellE, b->cellN,
                                             b->m.site_pairs_per_mol_pair, b->rep_obs);
     k_rep_kinetic<<<b->n_sys, 256, 0, st>>>(b->dgrids, b->n_sys, d.n, b->m, d, 0.5 * b->dt_last, b->rep_kin);
@@ -872,6 +822,8 @@ md_status md_batch_get_forces(md_batch *b, double *F, double *tau, int32_t on_de
     if (!b) return MD_ERR_ARG;
     if (!b->forces_valid) return MD_ERR_STATE;
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    md_status mf = batch_forces_to_f64(b, st);
+    if (mf != MD_OK) return mf;
     DevState &d = b->d;
     const double *src[2] = {d.F, d.tau};
     double *dst[2] = {F, tau}, *tmp[2] = {d.r2, d.v2};

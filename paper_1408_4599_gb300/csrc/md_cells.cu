@@ -5,21 +5,17 @@
 // what the force kernel reads.
 //
 // HBM-bound kernels: each reads/writes every molecule's record once.
-#include "md_internal.cuh"
+#include "md_leapfrog.cuh"
 
 #include <climits>
+
+using mdk::cell_coord;
 
 namespace {
 
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
-
-__device__ __forceinline__ int cell_axis(double x, double ell, int nc)
-{
-    int c = (int)floor(x / ell);
-    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
-}
 
 // Wrap positions into [0, L) and renormalise quaternions (input hygiene).
 __global__ void k_prepare(Grid g, double *r, double *q, long long n, int *flags)
@@ -57,9 +53,9 @@ __global__ void k_cellid(Grid g, const double *r, int *cell, int *count, long lo
 {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    int cx = cell_axis(r[3 * s], g.ell[0], g.nc[0]);
-    int cy = cell_axis(r[3 * s + 1], g.ell[1], g.nc[1]);
-    int cz = cell_axis(r[3 * s + 2], g.ell[2], g.nc[2]);
+    int cx = cell_coord(r[3 * s], g.iell[0], g.nc[0]);
+    int cy = cell_coord(r[3 * s + 1], g.iell[1], g.nc[1]);
+    int cz = cell_coord(r[3 * s + 2], g.iell[2], g.nc[2]);
     int c = (cz * g.nc[1] + cy) * g.nc[0] + cx;
     cell[s] = c;
     atomicAdd(&count[c], 1);

@@ -23,8 +23,12 @@ using namespace mdk;
 
 namespace {
 
+#ifndef MD_FORCE_MINB
+#define MD_FORCE_MINB 1
+#endif
+
 template <class SIG, bool HALF>
-__global__ void __launch_bounds__(MD_WARPS * 32) k_force(const __grid_constant__ ForceArgs A)
+__global__ void __launch_bounds__(MD_WARPS * 32, MD_FORCE_MINB) k_force(const __grid_constant__ ForceArgs A)
 {
     using Op = ForceOp<SIG, HALF>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -147,9 +151,7 @@ cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half
         e = cudaMemsetAsync(d.facc, 0, sizeof(float) * 6 * (d.n > 0 ? d.n : 1), s);
         if (e != cudaSuccess) return e;
     }
-    e = dispatch_sig(m, LaunchForce{A, half_shell, n_blocks, s});
-    if (e != cudaSuccess || !half_shell || d.n == 0) return e;
-    return launch_force_finalize(d, s);
+    return dispatch_sig(m, LaunchForce{A, half_shell, n_blocks, s});
 }
 
 cudaError_t launch_force_finalize(DevState &d, cudaStream_t s)

@@ -36,7 +36,7 @@ struct ForceOp {
     const ForceArgs &A;
     int K;
     int ig;
-    float pF0, pF1, pF2, pT0, pT1, pT2;
+    float pF0, pF1, pF2, pT0, pT1, pT2;            // the lane's pair of the current chunk (i side)
     float cU, cW, cX, cY, cZ;                      // pass sums of energy and virial (FP32)
     float sU, kU, sW, kW, sX, kX, sY, kY, sZ, kZ;  // compensated lane totals
     int nmol, nexam;
@@ -60,18 +60,17 @@ struct ForceOp {
 #pragma unroll
                 for (int q = 0; q < 6; q++) TT.x.jacc[q][t] = 0.f;
     }
-    __device__ void i_begin(const IMol<SIG> &, int) { pF0 = pF1 = pF2 = pT0 = pT1 = pT2 = 0.f; }
     __device__ void count_examined(int n) { nexam += n; }
-    __device__ void pair(Tile &TT, const IMol<SIG> &I, int k, float X0, float X1, float X2, int js, int)
+    __device__ void pair(Tile &TT, const IMol<SIG> &I, int k, float X0, float X1, float X2, int js, bool uniq)
     {
         float Fp[3], tp[3], tq[3], Up;
         mol_pair<SIG, HALF>(m, X0, X1, X2, I, A.geo + (long long)js * K, Fp, tp, tq, Up);
-        pF0 += Fp[0];
-        pF1 += Fp[1];
-        pF2 += Fp[2];
-        pT0 += tp[0];
-        pT1 += tp[1];
-        pT2 += tp[2];
+        pF0 = Fp[0];
+        pF1 = Fp[1];
+        pF2 = Fp[2];
+        pT0 = tp[0];
+        pT1 = tp[1];
+        pT2 = tp[2];
         cU += Up;
         cW += X0 * Fp[0] + X1 * Fp[1] + X2 * Fp[2];
         cX += X0 * Fp[0];
@@ -79,32 +78,42 @@ struct ForceOp {
         cZ += X2 * Fp[2];
         nmol++;
         if (HALF) {
-            TT.x.jacc[0][k] -= Fp[0];
-            TT.x.jacc[1][k] -= Fp[1];
-            TT.x.jacc[2][k] -= Fp[2];
-            TT.x.jacc[3][k] += tq[0];
-            TT.x.jacc[4][k] += tq[1];
-            TT.x.jacc[5][k] += tq[2];
+            // the Newton-3 reaction on j; a j that meets two i's of one chunk
+            // is the rare case that needs shared-memory atomics
+            float *J = &TT.x.jacc[0][0];
+            const float rv[6] = {-Fp[0], -Fp[1], -Fp[2], tq[0], tq[1], tq[2]};
+            if (uniq) {
+#pragma unroll
+                for (int q = 0; q < 6; q++) J[q * JCAP + k] += rv[q];
+            } else {
+#pragma unroll
+                for (int q = 0; q < 6; q++) atomicAdd(J + q * JCAP + k, rv[q]);
+            }
         }
     }
-    __device__ void i_end(const IMol<SIG> &, int il, int lane)
+    // i side of a chunk: a segmented suffix sum over the lanes (the pairs of
+    // one i are contiguous); the first lane of each i adds the i's total.
+    __device__ void chunk_end(Tile &, int il, bool valid, int lane)
     {
-        for (int msk = 16; msk > 0; msk >>= 1) {
-            pF0 += __shfl_xor_sync(FULLMASK, pF0, msk);
-            pF1 += __shfl_xor_sync(FULLMASK, pF1, msk);
-            pF2 += __shfl_xor_sync(FULLMASK, pF2, msk);
-            pT0 += __shfl_xor_sync(FULLMASK, pT0, msk);
-            pT1 += __shfl_xor_sync(FULLMASK, pT1, msk);
-            pT2 += __shfl_xor_sync(FULLMASK, pT2, msk);
+        float v[6] = {pF0, pF1, pF2, pT0, pT1, pT2};
+        if (!valid)
+#pragma unroll
+            for (int q = 0; q < 6; q++) v[q] = 0.f;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int ol = __shfl_down_sync(FULLMASK, il, off);
+            const bool take = lane + off < 32 && ol == il;
+#pragma unroll
+            for (int q = 0; q < 6; q++) {
+                const float o = __shfl_down_sync(FULLMASK, v[q], off);
+                if (take) v[q] += o;
+            }
         }
-        if (lane == 0) {
-            float *ip = T->x.ipart[il - ig];
-            ip[0] += pF0;
-            ip[1] += pF1;
-            ip[2] += pF2;
-            ip[3] += pT0;
-            ip[4] += pT1;
-            ip[5] += pT2;
+        const int prev = __shfl_up_sync(FULLMASK, il, 1);
+        if (valid && (lane == 0 || prev != il)) {
+            float *ip = T->x.ipart[il];
+#pragma unroll
+            for (int q = 0; q < 6; q++) ip[q] += v[q];
         }
     }
     __device__ void seg_end(Tile &TT, int nj, int lane)

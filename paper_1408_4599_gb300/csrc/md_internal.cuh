@@ -46,6 +46,7 @@ struct Grid {
     long long ncell;
     double L[3];
     double ell[3];                  // cell edge (>= rc)
+    double iell[3];                 // 1 / ell
     float ellf[3];
     double rc2;
     float rc2f;
@@ -96,9 +97,12 @@ cudaError_t launch_cellid(const Grid &g, DevState &d, cudaStream_t s);
 cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaStream_t s);
 cudaError_t launch_sort(long long ncell, DevState &d, cudaStream_t s);
 void swap_state(DevState &d);
+// half shell: the results stay in the FP32 accumulators d.facc until
+// launch_force_finalize; full shell: FP64 d.F, d.tau directly.
 cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half_shell, int n_blocks,
                          cudaStream_t s);
-cudaError_t launch_integrate(const Grid &g, const DevModel &m, DevState &d, double dt, cudaStream_t s);
+// acc32: read the forces from d.facc instead of d.F, d.tau
+cudaError_t launch_integrate(const Grid &g, const DevModel &m, DevState &d, double dt, int acc32, cudaStream_t s);
 cudaError_t launch_kinetic(const DevModel &m, DevState &d, double dt_half, int n_blocks, cudaStream_t s);
 cudaError_t launch_rescale(const DevModel &m, DevState &d, double fac_v, double fac_j, cudaStream_t s);
 cudaError_t launch_scatter_out(const DevState &d, const double *src, int width, double *dst, cudaStream_t s);

@@ -405,7 +405,10 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 }
 
 // ------------------------------------------------------------- traversal
-constexpr int JCAP = 256;   // staged candidates per segment
+#ifndef MD_JCAP
+#define MD_JCAP 256
+#endif
+constexpr int JCAP = MD_JCAP;  // staged candidates per segment (a multiple of 32)
 constexpr int QCAP = 64;    // hit queue
 
 // Per-warp staging area; Extra is the pair operation's own shared state.
@@ -428,13 +431,19 @@ struct GridView {
 };
 
 // Visits every interacting pair (i in cell c, j in the stencil) in chunks
-// of <= 32 pairs of one i.  Op provides:
+// of <= 32 pairs.  The hits of consecutive i molecules of a pass share a
+// queue, so a chunk may hold pairs of several i's (contiguous lanes per i,
+// in i order) and only the last chunk of a segment is partly filled.
+// Op provides:
+//   pass_begin(ig, ni, lane) / pass_end(s0, ig, ni, lane)
 //   seg_begin(T, nj, lane)            after a segment has been staged
 //   seg_end(T, nj, lane)              after all i's of a pass met the segment
-//   i_begin(I, il)                    before the candidates of one i
-//   pair(T, I, k, X0, X1, X2, lane)   for the lane's queued pair (lane < nq)
-//   i_end(I, il, lane)                after the candidates of one i
-//   pass_begin(ig, ni, lane) / pass_end(s0, ig, ni, lane)
+//   pair(T, I, k, X0, X1, X2, js, uniq)
+//                                     the lane's queued pair (i molecule I,
+//                                     staged candidate k, storage slot js);
+//                                     uniq: no other lane of the chunk has k
+//   chunk_end(T, il, valid, lane)     all lanes, after the pairs of a chunk;
+//                                     il = the lane's i index in the pass
 //   count_examined(n)
 // cell_start holds global slots; c is the cell index inside the grid.
 template <class SIG, bool HALF, class Op, class Extra>
@@ -444,6 +453,7 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
                                               Op &op, int lane)
 {
     constexpr int IMAX = Op::IMAX;
+    static_assert(IMAX <= 32 && JCAP <= 65536, "queue entry packs (i << 16) | k");
     const int s0 = cell_start[g.cell0 + c];
     const int n_i = cell_start[g.cell0 + c + 1] - s0;
     if (n_i == 0) return;
@@ -455,6 +465,25 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
     for (int ig = 0; ig < n_i; ig += IMAX) {
         const int ni = min(IMAX, n_i - ig);
         op.pass_begin(ig, ni, lane);
+        // the first nq queue entries as one chunk (all lanes call)
+        auto chunk = [&](int nq) {
+            const bool valid = lane < nq;
+            int il = 32 + lane, k = -1 - lane;  // unique placeholders for idle lanes
+            if (valid) {
+                const int e = T.queue[lane];
+                il = e >> 16;
+                k = e & 0xffff;
+            }
+            bool uniq = true;
+            if (HALF) uniq = __match_any_sync(FULLMASK, k) == (1u << lane);
+            if (valid) {
+                IMol<SIG> I;
+                load_i<SIG>(m, com, geo, K, s0 + ig + il, I);
+                const float4 cj = T.jc[k];
+                op.pair(T, I, k, I.c.x - cj.x, I.c.y - cj.y, I.c.z - cj.z, __float_as_int(cj.w), uniq);
+            }
+            op.chunk_end(T, il, valid, lane);
+        };
         int o_cur = 0, o_pos = 0;
         while (o_cur < NOFF) {
             int nj = 0, self_lo = 0, self_n = 0, self_base = 0;
@@ -488,20 +517,20 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
             }
             op.seg_begin(T, nj, lane);
             __syncwarp();
+            int qn = 0;
             for (int il = ig; il < ig + ni; il++) {
-                IMol<SIG> I;
-                load_i<SIG>(m, com, geo, K, s0 + il, I);
-                op.i_begin(I, il);
+                const int si = s0 + il;
+                const float4 ci = com[si];
                 const int skip_to = (self_n > 0 && HALF) ? max(0, min(self_n, il - self_lo + 1)) : 0;
                 const int self_k =
                     (self_n > 0 && !HALF && il >= self_lo && il < self_lo + self_n) ? self_base + (il - self_lo) : -1;
-                int qn = 0;
+                const int tag = (il - ig) << 16;
                 for (int kb = skip_to; kb < nj; kb += 32) {
                     const int k = kb + lane;
                     bool hit = false;
                     if (k < nj && k != self_k) {
                         const float4 cj = T.jc[k];
-                        const float X0 = I.c.x - cj.x, X1 = I.c.y - cj.y, X2 = I.c.z - cj.z;
+                        const float X0 = ci.x - cj.x, X1 = ci.y - cj.y, X2 = ci.z - cj.z;
                         const float d2 = X0 * X0 + X1 * X1 + X2 * X2;
                         hit = d2 < g.rc2f;
                         if (fabsf(d2 - g.rc2f) < g.bandf) {
@@ -510,7 +539,7 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
                             wrap_axis(cx, dx, g.nc[0], kx);
                             wrap_axis(cy, dy, g.nc[1], ky);
                             wrap_axis(cz, dz, g.nc[2], kz);
-                            const double *ri = r64 + 3LL * I.slot, *rj = r64 + 3LL * __float_as_int(cj.w);
+                            const double *ri = r64 + 3LL * si, *rj = r64 + 3LL * __float_as_int(cj.w);
                             const double e0 = __dsub_rn(__dsub_rn(ri[0], rj[0]), (double)kx * g.L[0]);
                             const double e1 = __dsub_rn(__dsub_rn(ri[1], rj[1]), (double)ky * g.L[1]);
                             const double e2 = __dsub_rn(__dsub_rn(ri[2], rj[2]), (double)kz * g.L[2]);
@@ -518,29 +547,22 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
                         }
                     }
                     const unsigned bal = __ballot_sync(FULLMASK, hit);
-                    if (hit) T.queue[qn + __popc(bal & lt_mask)] = k;
+                    if (hit) T.queue[qn + __popc(bal & lt_mask)] = tag | k;
                     qn += __popc(bal);
                     if (qn >= 32) {
                         __syncwarp();
-                        const int kq = T.queue[lane];
-                        const float4 cj = T.jc[kq];
-                        op.pair(T, I, kq, I.c.x - cj.x, I.c.y - cj.y, I.c.z - cj.z, __float_as_int(cj.w), lane);
+                        chunk(32);
                         __syncwarp();
                         if (lane < qn - 32) T.queue[lane] = T.queue[32 + lane];
                         qn -= 32;
+                        __syncwarp();
                     }
-                }
-                if (qn > 0) {
-                    __syncwarp();
-                    if (lane < qn) {
-                        const int kq = T.queue[lane];
-                        const float4 cj = T.jc[kq];
-                        op.pair(T, I, kq, I.c.x - cj.x, I.c.y - cj.y, I.c.z - cj.z, __float_as_int(cj.w), lane);
-                    }
-                    __syncwarp();
                 }
                 if (lane == 0) op.count_examined(nj - skip_to - (self_k >= 0 ? 1 : 0));
-                op.i_end(I, il, lane);
+            }
+            if (qn > 0) {
+                __syncwarp();
+                chunk(qn);
             }
             __syncwarp();
             op.seg_end(T, nj, lane);

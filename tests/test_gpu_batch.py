@@ -83,17 +83,23 @@ def test_batch_equals_single_systems():
 
 def test_graph_replay_equals_eager_steps():
     cfgs = _replicas(n_rep=5, seed_k=7)
-    res = []
+    res, obs = [], []
     for use_graph in (False, True):
         b = md.Batch(cfgs, half_shell=0).set()
         b.step(5, 0.001, use_graph=use_graph)   # 2 graph replays + 1 eager step
-        b.step(4, 0.001, use_graph=use_graph)   # other buffer parity
+        o5 = b.observables()
+        b.step(4, 0.001, use_graph=use_graph)   # other buffer parity; replays graphs captured above
         res.append(b.molecules())
         o = b.observables()
         assert all(x["step"] == 9 for x in o)
+        obs.append(o5 + o)
         b.close()
     for a, c in zip(res[0], res[1]):
         assert np.array_equal(a, c)
+    # the observables after a replay come from that replay's forces (no stale FP64 copy)
+    for a, c in zip(obs[0], obs[1]):
+        for k in ("U_pot", "W", "K_trans", "K_rot", "n_mol_pairs"):
+            assert a[k] == c[k], k
 
 
 def test_tuner_and_nve_energy():
