@@ -71,6 +71,7 @@ def _lib_handle():
         lib.orc_forces.argtypes = [P(Model), P(Setup), i64, dp, dp, i32, i32, dp, dp, dp]
         lib.orc_forces_subset.argtypes = [P(Model), P(Setup), i64, dp, dp, i64, P(i64), i32, dp, dp]
         lib.orc_step.argtypes = [P(Model), P(Setup), i64, d, i32, i32, i32, dp, dp, dp, dp, dp, dp, dp]
+        lib.orc_step_T.argtypes = [P(Model), P(Setup), i64, d, i32, d, i32, i32, dp, dp, dp, dp, dp, dp, dp]
         lib.orc_kinetic.argtypes = [P(Model), i64, d, dp, dp, dp, dp, dp, dp]
         lib.orc_lrc.argtypes = [P(Model), P(Setup), i64, dp]
         lib.orc_n_params.argtypes = [P(Model)]
@@ -187,9 +188,10 @@ def forces_subset(model: dict, setup: Setup, r, q, sel, n_threads: int = 0):
 
 
 def step(model: dict, setup: Setup, state: dict, dt: float, n_steps: int, use_cells: bool = False,
-         n_threads: int = 0):
+         n_threads: int = 0, T_target: float = 0.0):
     """Advance a copy of ``state`` (r, v, q, j and optionally F, tau) by
-    n_steps leapfrog steps; returns the new state dict with F, tau, obs."""
+    n_steps leapfrog steps; returns the new state dict with F, tau, obs.
+    T_target > 0: velocity rescaling to T_target after every step (orc_step_T)."""
     lib = _lib_handle()
     r = _c(state["r"]).copy()
     v = _c(state["v"]).copy()
@@ -202,8 +204,8 @@ def step(model: dict, setup: Setup, state: dict, dt: float, n_steps: int, use_ce
         F, tau, _ = forces(model, setup, r, q, use_cells, n_threads)
     obs = np.zeros(NOBS)
     M = make_model(model)
-    rc = lib.orc_step(C.byref(M), C.byref(setup), r.shape[0], float(dt), int(n_steps), int(use_cells),
-                      int(n_threads), _dp(r), _dp(v), _dp(q), _dp(j), _dp(F), _dp(tau), _dp(obs))
+    rc = lib.orc_step_T(C.byref(M), C.byref(setup), r.shape[0], float(dt), int(n_steps), float(T_target),
+                        int(use_cells), int(n_threads), _dp(r), _dp(v), _dp(q), _dp(j), _dp(F), _dp(tau), _dp(obs))
     if rc != 0:
         raise ValueError(f"orc_step failed with code {rc}")
     out = {"r": r, "v": v, "q": q, "j": j, "F": F, "tau": tau}

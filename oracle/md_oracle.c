@@ -749,6 +749,46 @@ static void normalise4(double *q)
 int orc_step(const orc_model *m, const orc_setup *s, int64_t n, double dt, int n_steps, int use_cells, int n_threads,
              double *r, double *v, double *q, double *j, double *F, double *tau, double *obs)
 {
+    return orc_step_T(m, s, n, dt, n_steps, 0.0, use_cells, n_threads, r, v, q, j, F, tau, obs);
+}
+
+/* Canonical ensemble by velocity rescaling (§2, ensembles paragraph: the
+ * temperature of NVT runs is kept constant by rescaling the velocities).
+ * Reading taken: after the leapfrog update of every molecule, the kinetic
+ * temperature of the half-step state,
+ *   T_half = 2 (K_trans + K_rot) / dof,  dof = 3N - 3 + N * (rotational dof),
+ *   K_trans = sum 1/2 m v(t+dt/2)^2,
+ *   K_rot   = sum 1/2 w.I w,  w = I^-1 A(q(t+dt)) j(t+dt/2),
+ * is brought to T_target by scaling v and j of every molecule by the one
+ * factor sqrt(T_target / T_half); positions and orientations of the step
+ * are not changed.  T_target <= 0 (or T_half = 0) leaves the state as is. */
+static void rescale_to(const orc_model *m, int64_t n, double T_target, double *v, const double *q, double *j)
+{
+    double mass, Iinv[3], I[3];
+    model_inertia(m, &mass, Iinv, I);
+    const int rot = (I[0] > 1e-12) + (I[1] > 1e-12) + (I[2] > 1e-12);
+    const double dof = 3.0 * (double)n - 3.0 + (double)rot * (double)n;
+    double kt = 0.0, kr = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double w[3];
+        kt += 0.5 * mass * dot3(&v[3 * i], &v[3 * i]);
+        omega_body(&q[4 * i], &j[3 * i], Iinv, w);
+        for (int k = 0; k < 3; k++) kr += 0.5 * I[k] * w[k] * w[k];
+    }
+    if (!(dof > 0.0)) return;
+    const double T = 2.0 * (kt + kr) / dof;
+    if (!(T > 0.0)) return;
+    const double beta = sqrt(T_target / T);
+    for (int64_t i = 0; i < 3 * n; i++) {
+        v[i] *= beta;
+        j[i] *= beta;
+    }
+}
+
+int orc_step_T(const orc_model *m, const orc_setup *s, int64_t n, double dt, int n_steps, double T_target,
+               int use_cells, int n_threads, double *r, double *v, double *q, double *j, double *F, double *tau,
+               double *obs)
+{
     double mass, Iinv[3], I[3];
     model_inertia(m, &mass, Iinv, I);
     for (int st = 0; st < n_steps; st++) {
@@ -772,6 +812,7 @@ int orc_step(const orc_model *m, const orc_setup *s, int64_t n, double dt, int n
             for (int k = 0; k < 4; k++) qi[k] += dt * qd[k];
             normalise4(qi);
         }
+        if (T_target > 0.0) rescale_to(m, n, T_target, v, q, j);
         int rcode = forces_impl(m, s, n, r, q, use_cells, n_threads, F, tau, obs, NULL, NULL, NULL, NULL);
         if (rcode) return rcode;
     }

@@ -77,6 +77,10 @@ int orc_forces_subset(const orc_model *m, const orc_setup *s, int64_t n, const d
                       int64_t n_sel, const int64_t *sel, int n_threads, double *F, double *tau);
 int orc_step(const orc_model *m, const orc_setup *s, int64_t n, double dt, int n_steps, int use_cells,
              int n_threads, double *r, double *v, double *q, double *j, double *F, double *tau, double *obs);
+/* orc_step with the velocity-rescaling thermostat (T_target > 0; <= 0: NVE) */
+int orc_step_T(const orc_model *m, const orc_setup *s, int64_t n, double dt, int n_steps, double T_target,
+               int use_cells, int n_threads, double *r, double *v, double *q, double *j, double *F, double *tau,
+               double *obs);
 int orc_kinetic(const orc_model *m, int64_t n, double dt, const double *v, const double *q, const double *j,
                 const double *F, const double *tau, double *K);
 int orc_lrc(const orc_model *m, const orc_setup *s, int64_t n, double *out);

@@ -546,3 +546,72 @@ def test_energy_fluctuation_scales_as_dt_squared():
         assert np.abs(Lang - Lang[0]).max() < 1e-9 * max(1.0, np.abs(Lang).max())
     ratio = res[0] / res[1]
     assert 3.0 < ratio < 5.0, ratio
+
+
+# ------------------------------------------- NVT velocity rescaling (§2)
+def _rot_axis_angle_form(q):
+    """R(q) as (w^2 - |u|^2) 1 + 2 u u^T + 2 w [u]x, built independently of
+    the oracle's element-wise matrix."""
+    w, u = q[0], np.asarray(q[1:], dtype=np.float64)
+    ux = np.array([[0.0, -u[2], u[1]], [u[2], 0.0, -u[0]], [-u[1], u[0], 0.0]])
+    return (w * w - u @ u) * np.eye(3) + 2.0 * np.outer(u, u) + 2.0 * w * ux
+
+
+def _half_step_temperature(model, v, q, j):
+    """2 (K_trans + K_rot) / dof of the stored half-step state, with
+    K_rot = sum_k b_k^2 / (2 I_k) over the non-zero principal moments
+    (b = body-frame angular momentum)."""
+    m = sum(s["mass"] for s in model["lj"])
+    In = np.zeros((3, 3))
+    for s in model["lj"]:
+        p = np.asarray(s["pos"], dtype=np.float64)
+        In += s["mass"] * ((p @ p) * np.eye(3) - np.outer(p, p))
+    assert np.abs(In - np.diag(np.diag(In))).max() < 1e-12  # body frame = principal frame
+    I = np.diag(In)
+    live = I > 1e-12
+    kt = 0.5 * m * (v * v).sum()
+    kr = 0.0
+    for qi, ji in zip(q, j):
+        b = _rot_axis_angle_form(qi).T @ ji
+        kr += 0.5 * (b[live] ** 2 / I[live]).sum()
+    n = v.shape[0]
+    dof = 3 * n - 3 + int(live.sum()) * n
+    return 2.0 * (kt + kr) / dof
+
+
+@pytest.mark.parametrize("which", ["2cljq", "4site"])
+def test_velocity_rescaling_reaches_target(which):
+    """After every thermostatted step the half-step kinetic temperature
+    (translation + rotation, dof = 3N - 3 + N rot. dof) equals T_target."""
+    if which == "2cljq":
+        cfg = mdgen.config_2cljq(n=400, rho=0.3)
+    else:
+        cfg = mdgen.config_4site(n=300, rho=0.3)
+    s = oracle.setup_from_config(cfg)
+    st = {k: cfg[k] for k in ("r", "v", "q", "j")}
+    T0 = _half_step_temperature(cfg["model"], st["v"], st["q"], st["j"])
+    for T_target in (0.7, 1.6):
+        cur = st
+        for _ in range(3):
+            cur = oracle.step(cfg["model"], s, cur, cfg["dt"], 1, T_target=T_target)
+            T = _half_step_temperature(cfg["model"], cur["v"], cur["q"], cur["j"])
+            assert T == pytest.approx(T_target, rel=1e-12), (T, T_target, T0)
+
+
+def test_velocity_rescaling_is_one_common_factor_after_the_update():
+    """One thermostatted step = the NVE step (same positions, orientations
+    and new forces) with v and j of every molecule scaled by one factor."""
+    cfg = mdgen.config_4site(n=300, rho=0.3)
+    s = oracle.setup_from_config(cfg)
+    st = {k: cfg[k] for k in ("r", "v", "q", "j")}
+    a = oracle.step(cfg["model"], s, st, cfg["dt"], 1)
+    b = oracle.step(cfg["model"], s, st, cfg["dt"], 1, T_target=2.5)
+    assert np.array_equal(a["r"], b["r"]) and np.array_equal(a["q"], b["q"])
+    assert np.array_equal(a["F"], b["F"]) and np.array_equal(a["tau"], b["tau"])
+    ratio_v = b["v"] / a["v"]
+    ratio_j = b["j"] / a["j"]
+    beta = ratio_v.flat[0]
+    assert beta > 1.0
+    assert np.allclose(ratio_v, beta, rtol=1e-14, atol=0) and np.allclose(ratio_j, beta, rtol=1e-14, atol=0)
+    T_nve = _half_step_temperature(cfg["model"], a["v"], a["q"], a["j"])
+    assert beta == pytest.approx(math.sqrt(2.5 / T_nve), rel=1e-12)
