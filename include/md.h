@@ -152,9 +152,13 @@ md_status md_compute_forces(md_system *sys, void *cuda_stream);
 
 /* n_steps leapfrog steps of size dt (Eqs. 2-5): half-kick/drift/rotate
  * with the current forces, wrap, rebuild cells, recompute forces.
- * T_target <= 0: NVE.  T_target > 0: velocity rescaling to T_target after
- * every step (§2 NVT).  Computes forces first if they are stale.
- * Asynchronous. */
+ * T_target <= 0: NVE.  T_target > 0: NVT by velocity rescaling (§2,
+ * ensembles): after the update of each step, v and j of every molecule are
+ * scaled by sqrt(T_target / T_half), T_half = 2 (K_trans + K_rot) / dof of
+ * the half-step state (v, j at t + dt/2, q at t + dt; dof = 3N - 3 + N x
+ * rotational dof); positions and orientations of the step are unchanged.
+ * Computes forces first if they are stale.  Asynchronous (the factor is
+ * computed and applied on the device). */
 md_status md_step(md_system *sys, int32_t n_steps, double dt, double T_target, void *cuda_stream);
 
 /* Synchronising read-back of the observables at the current time t:

@@ -477,7 +477,7 @@ void free_all(md_system *s)
     DevState &d = s->d;
     void *ptrs[] = {d.r, d.v, d.q, d.j, d.r2, d.v2, d.q2, d.j2, d.ids, d.ids2, d.F, d.tau, d.cell, d.cell_count,
                     d.cell_start, d.cell_fill, d.perm, d.perm2, d.com, d.geo, d.scan_tmp, d.partials,
-                    d.kin_partials, d.flags, d.facc, s->adj_partials};
+                    d.kin_partials, d.thermo, d.flags, d.facc, s->adj_partials};
     for (void *p : ptrs) cudaFree(p);
     for (auto &p : s->pending) {
         cudaEventDestroy(p.a);
@@ -505,11 +505,11 @@ md_status check_flags(md_system *s)
     return MD_OK;
 }
 
-md_status do_rebuild(md_system *s, cudaStream_t st, bool need_cellid)
+md_status do_rebuild(md_system *s, cudaStream_t st, bool need_cellid, const double *beta = nullptr)
 {
     TimeScope ts(s, st, 1);
     if (need_cellid) CK(launch_cellid(s->g, s->d, st), "cell id kernel");
-    CK(launch_rebuild(s->g, s->m, s->d, st), "cell rebuild kernels");
+    CK(launch_rebuild(s->g, s->m, s->d, st, beta), "cell rebuild kernels");
     s->binned = true;
     return MD_OK;
 }
@@ -622,6 +622,7 @@ md_status md_create(const double box[3], double cutoff, const md_site_types *typ
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.scan_tmp, sizeof(int) * (scan_blocks(ncell) + 1));
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.partials, sizeof(double) * P_COUNT * s->n_force_blocks);
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.kin_partials, sizeof(double) * 4 * s->n_kin_blocks);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.thermo, sizeof(double) * 2);
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.flags, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMemset(d.flags, 0, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaMemset(d.cell_start, 0, sizeof(int) * (ncell + 1));
@@ -737,10 +738,6 @@ md_status md_step(md_system *s, int32_t n_steps, double dt, double T_target, voi
         set_err(s, "md_step: call md_set_molecules first");
         return MD_ERR_STATE;
     }
-    if (T_target > 0.0) {
-        set_err(s, "md_step: velocity-rescaling NVT is not built yet; pass T_target <= 0 (NVE)");
-        return MD_ERR_UNSUPPORTED;
-    }
     if (!(s->m.mass > 0.0)) {
         set_err(s, "md_step: the component has no mass");
         return MD_ERR_STATE;
@@ -751,12 +748,17 @@ md_status md_step(md_system *s, int32_t n_steps, double dt, double T_target, voi
         md_status ms = md_compute_forces(s, st);
         if (ms != MD_OK) return ms;
     }
+    // NVT (§2): velocity rescaling after every step, folded into the reorder
+    const bool nvt = T_target > 0.0;
+    const double dof = 3.0 * (double)s->d.n - 3.0 + (double)s->m.rot_dof * (double)s->d.n;
     for (int k = 0; k < n_steps; k++) {
         {
             TimeScope ts(s, st, 0);
             CK(launch_integrate(s->g, s->m, s->d, dt, s->f_in_acc ? 1 : 0, st), "integrate kernel");
+            if (nvt && dof > 0.0 && s->d.n > 0)
+                CK(launch_thermostat(s->m, s->d, s->n_kin_blocks, T_target, dof, st), "thermostat kernels");
         }
-        md_status ms = do_rebuild(s, st, false);
+        md_status ms = do_rebuild(s, st, false, nvt && dof > 0.0 && s->d.n > 0 ? s->d.thermo : nullptr);
         if (ms != MD_OK) return ms;
         ms = do_force(s, st);
         if (ms != MD_OK) return ms;

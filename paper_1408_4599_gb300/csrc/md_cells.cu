@@ -173,18 +173,19 @@ __global__ void k_sort_cells(const int *start, const int *perm, const int *ids, 
 // of the force kernel: the centre of mass relative to its cell centre
 // (formed in FP64, then rounded) and the space-frame site offsets and axes
 // R(q) d, R(q) e.
-__global__ void k_reorder_pack(Grid g, DevModel m, DevState d)
+__global__ void k_reorder_pack(Grid g, DevModel m, DevState d, const double *beta)
 {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= d.n) return;
     int o = d.perm2[s];
+    const double b = beta ? *beta : 1.0;  // velocity-rescaling factor of this step
     double rx = d.r[3 * o], ry = d.r[3 * o + 1], rz = d.r[3 * o + 2];
     d.r2[3 * s] = rx;
     d.r2[3 * s + 1] = ry;
     d.r2[3 * s + 2] = rz;
     for (int k = 0; k < 3; k++) {
-        d.v2[3 * s + k] = d.v[3 * o + k];
-        d.j2[3 * s + k] = d.j[3 * o + k];
+        d.v2[3 * s + k] = b * d.v[3 * o + k];
+        d.j2[3 * s + k] = b * d.j[3 * o + k];
     }
     double qw = d.q[4 * o], qx = d.q[4 * o + 1], qy = d.q[4 * o + 2], qz = d.q[4 * o + 3];
     d.q2[4 * s] = qw;
@@ -281,11 +282,11 @@ void swap_state(DevState &d)
 
 // Scan of the histogram, scatter, in-cell sort, reorder + pack, then swap
 // the state buffers.  Expects cell[] and cell_count[] of the current order.
-cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaStream_t s)
+cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaStream_t s, const double *beta)
 {
     cudaError_t e = launch_sort(g.ncell, d, s);
     if (e != cudaSuccess) return e;
-    if (d.n > 0) k_reorder_pack<<<nblk(d.n, 256), 256, 0, s>>>(g, m, d);
+    if (d.n > 0) k_reorder_pack<<<nblk(d.n, 256), 256, 0, s>>>(g, m, d, beta);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     double *t;

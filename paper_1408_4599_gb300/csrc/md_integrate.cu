@@ -75,6 +75,60 @@ __global__ void k_kinetic(DevModel m, DevState d, double dt_half)
     }
 }
 
+// Velocity rescaling (§2: NVT by rescaling the velocities), step 1: the
+// half-step kinetic energies K_trans = sum 1/2 m v^2 (FP64) and
+// K_rot = sum 1/2 w.I w with w = I^-1 A(q) j from the rounded state (FP32
+// per molecule, FP64 sums), v, j at t + dt/2 and q at t + dt.  Block
+// partials in kin_partials[4b + 2], [4b + 3].
+__global__ void k_kinetic_half(DevModel m, DevState d)
+{
+    __shared__ double sh[2][32];
+    double kt = 0.0, kr = 0.0;
+    const float Iinv[3] = {(float)m.Iinv[0], (float)m.Iinv[1], (float)m.Iinv[2]};
+    const float Im[3] = {(float)m.I[0], (float)m.I[1], (float)m.I[2]};
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < d.n; s += (long long)gridDim.x * blockDim.x) {
+        const double v0 = d.v[3 * s], v1 = d.v[3 * s + 1], v2 = d.v[3 * s + 2];
+        kt += v0 * v0 + v1 * v1 + v2 * v2;
+        if (m.rot_dof > 0) {
+            const float qf[4] = {(float)d.q[4 * s], (float)d.q[4 * s + 1], (float)d.q[4 * s + 2], (float)d.q[4 * s + 3]};
+            const float jf[3] = {(float)d.j[3 * s], (float)d.j[3 * s + 1], (float)d.j[3 * s + 2]};
+            float w[3];
+            omega_body_f(qf, jf, Iinv, w);
+            kr += (double)(Im[0] * w[0] * w[0] + Im[1] * w[1] * w[1] + Im[2] * w[2] * w[2]);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        kt += __shfl_xor_sync(0xffffffffu, kt, o);
+        kr += __shfl_xor_sync(0xffffffffu, kr, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][warp] = kt;
+        sh[1][warp] = kr;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[threadIdx.x][w];
+        d.kin_partials[blockIdx.x * 4 + 2 + threadIdx.x] = 0.5 * (threadIdx.x == 0 ? m.mass : 1.0) * t;
+    }
+}
+
+// Step 2 (one warp, fixed summation order): T_half = 2 (K_trans + K_rot) /
+// dof and the factor sqrt(T_target / T_half) (1 if T_half is not positive).
+__global__ void k_thermo_factor(DevState d, int n_blocks, double T_target, double dof)
+{
+    const int lane = threadIdx.x;
+    double k = 0.0;
+    for (int b = lane; b < n_blocks; b += 32) k += d.kin_partials[4 * b + 2] + d.kin_partials[4 * b + 3];
+    for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+    if (lane == 0) {
+        const double T = 2.0 * k / dof;
+        d.thermo[0] = (T > 0.0 && isfinite(T)) ? sqrt(T_target / T) : 1.0;
+        d.thermo[1] = T;
+    }
+}
+
 __global__ void k_rescale(DevState d, double fv, double fj)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -99,6 +153,15 @@ cudaError_t launch_integrate(const Grid &g, const DevModel &m, DevState &d, doub
 cudaError_t launch_kinetic(const DevModel &m, DevState &d, double dt_half, int n_blocks, cudaStream_t s)
 {
     k_kinetic<<<n_blocks, 256, 0, s>>>(m, d, dt_half);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_thermostat(const DevModel &m, DevState &d, int n_blocks, double T_target, double dof, cudaStream_t s)
+{
+    k_kinetic_half<<<n_blocks, 256, 0, s>>>(m, d);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_thermo_factor<<<1, 32, 0, s>>>(d, n_blocks, T_target, dof);
     return cudaGetLastError();
 }
 

@@ -71,7 +71,8 @@ struct DevState {
     float4 *geo;                    // n * K: site offsets then axes (space frame)
     int *scan_tmp;                  // block sums of the scan
     double *partials;               // force-kernel block partials, 8 per block
-    double *kin_partials;           // kinetic partials, 4 per block
+    double *kin_partials;           // kinetic partials, 4 per block ([2], [3]: half-step K for the thermostat)
+    double *thermo;                 // [0] velocity-rescaling factor of the last step, [1] its T_half
     int *flags;                     // [0] non-finite, [1] overflow, [2] timeout
     float *facc;                    // 6 x n FP32 force/torque accumulators (half shell)
 };
@@ -94,7 +95,9 @@ enum { FLAG_NONFINITE = 0, FLAG_OVERFLOW = 1, FLAG_TIMEOUT = 2 };
 // ------------------------------------------------------------- launchers
 // (all return cudaGetLastError() of the launch)
 cudaError_t launch_cellid(const Grid &g, DevState &d, cudaStream_t s);
-cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaStream_t s);
+// beta (device scalar, may be NULL): factor applied to v and j while they are reordered
+cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaStream_t s,
+                           const double *beta = nullptr);
 cudaError_t launch_sort(long long ncell, DevState &d, cudaStream_t s);
 void swap_state(DevState &d);
 // half shell: the results stay in the FP32 accumulators d.facc until
@@ -105,6 +108,9 @@ cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half
 cudaError_t launch_integrate(const Grid &g, const DevModel &m, DevState &d, double dt, int acc32, cudaStream_t s);
 cudaError_t launch_kinetic(const DevModel &m, DevState &d, double dt_half, int n_blocks, cudaStream_t s);
 cudaError_t launch_rescale(const DevModel &m, DevState &d, double fac_v, double fac_j, cudaStream_t s);
+// velocity rescaling to T_target: half-step kinetic energies -> d.thermo[0] = sqrt(T_target / T_half)
+cudaError_t launch_thermostat(const DevModel &m, DevState &d, int n_blocks, double T_target, double dof,
+                              cudaStream_t s);
 cudaError_t launch_scatter_out(const DevState &d, const double *src, int width, double *dst, cudaStream_t s);
 cudaError_t launch_gather_in(DevState &d, const double *src, int width, double *dst, cudaStream_t s);
 cudaError_t launch_prepare_input(const Grid &g, DevState &d, cudaStream_t s);

@@ -409,7 +409,7 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 #define MD_JCAP 256
 #endif
 constexpr int JCAP = MD_JCAP;  // staged candidates per segment (a multiple of 32)
-constexpr int QCAP = 64;    // hit queue
+constexpr int QCAP = 96;    // hit queue (31 waiting + 2 x 32 new)
 
 // Per-warp staging area; Extra is the pair operation's own shared state.
 template <class Extra>
@@ -458,10 +458,28 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
     const int n_i = cell_start[g.cell0 + c + 1] - s0;
     if (n_i == 0) return;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const int NOFF = HALF ? 14 : 27;
+    constexpr int NOFF = HALF ? 14 : 27;
+    constexpr int SELF = HALF ? 0 : 13;  // stencil index of the cell itself
     const int cx = (int)(c % g.nc[0]);
     const int cy = (int)((c / g.nc[0]) % g.nc[1]);
     const int cz = (int)(c / ((long long)g.nc[0] * g.nc[1]));
+    // stencil cell of lane t (< NOFF): first slot, count, image offset; all
+    // loaded at once, then broadcast by shuffles while staging
+    int t_j0 = 0, t_cnt = 0;
+    float t_ox = 0.f, t_oy = 0.f, t_oz = 0.f;
+    if (lane < NOFF) {
+        int dx, dy, dz, kx, ky, kz;
+        stencil_offset(HALF, lane, dx, dy, dz);
+        const int nx = wrap_axis(cx, dx, g.nc[0], kx);
+        const int ny = wrap_axis(cy, dy, g.nc[1], ky);
+        const int nz = wrap_axis(cz, dz, g.nc[2], kz);
+        const long long cn = g.cell0 + ((long long)nz * g.nc[1] + ny) * g.nc[0] + nx;
+        t_j0 = cell_start[cn];
+        t_cnt = cell_start[cn + 1] - t_j0;
+        t_ox = dx * g.ellf[0];
+        t_oy = dy * g.ellf[1];
+        t_oz = dz * g.ellf[2];
+    }
     for (int ig = 0; ig < n_i; ig += IMAX) {
         const int ni = min(IMAX, n_i - ig);
         op.pass_begin(ig, ni, lane);
@@ -488,20 +506,15 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
         while (o_cur < NOFF) {
             int nj = 0, self_lo = 0, self_n = 0, self_base = 0;
             while (o_cur < NOFF && nj < JCAP) {
-                int dx, dy, dz, kx, ky, kz;
-                stencil_offset(HALF, o_cur, dx, dy, dz);
-                const int nx = wrap_axis(cx, dx, g.nc[0], kx);
-                const int ny = wrap_axis(cy, dy, g.nc[1], ky);
-                const int nz = wrap_axis(cz, dz, g.nc[2], kz);
-                const long long cn = g.cell0 + ((long long)nz * g.nc[1] + ny) * g.nc[0] + nx;
-                const int j0 = cell_start[cn], cnt = cell_start[cn + 1] - j0;
+                const int j0 = __shfl_sync(FULLMASK, t_j0, o_cur), cnt = __shfl_sync(FULLMASK, t_cnt, o_cur);
+                const float ox = __shfl_sync(FULLMASK, t_ox, o_cur), oy = __shfl_sync(FULLMASK, t_oy, o_cur),
+                            oz = __shfl_sync(FULLMASK, t_oz, o_cur);
                 const int take = min(cnt - o_pos, JCAP - nj);
-                if (dx == 0 && dy == 0 && dz == 0) {  // the i-cell: local index self_lo + (k - self_base)
+                if (o_cur == SELF) {  // the i-cell: local index self_lo + (k - self_base)
                     self_lo = o_pos;
                     self_n = take;
                     self_base = nj;  // 0 in the half shell (stencil index 0 opens a segment)
                 }
-                const float ox = dx * g.ellf[0], oy = dy * g.ellf[1], oz = dz * g.ellf[2];
                 for (int t = lane; t < take; t += 32) {
                     const int js = j0 + o_pos + t;
                     const float4 cj = com[js];
@@ -520,40 +533,52 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
             int qn = 0;
             for (int il = ig; il < ig + ni; il++) {
                 const int si = s0 + il;
-                const float4 ci = com[si];
+                const bool in_seg = self_n > 0 && il >= self_lo && il < self_lo + self_n;
+                const float4 ci = in_seg ? T.jc[self_base + il - self_lo] : com[si];
                 const int skip_to = (self_n > 0 && HALF) ? max(0, min(self_n, il - self_lo + 1)) : 0;
-                const int self_k =
-                    (self_n > 0 && !HALF && il >= self_lo && il < self_lo + self_n) ? self_base + (il - self_lo) : -1;
+                const int self_k = (!HALF && in_seg) ? self_base + (il - self_lo) : -1;
                 const int tag = (il - ig) << 16;
-                for (int kb = skip_to; kb < nj; kb += 32) {
-                    const int k = kb + lane;
-                    bool hit = false;
-                    if (k < nj && k != self_k) {
-                        const float4 cj = T.jc[k];
-                        const float X0 = ci.x - cj.x, X1 = ci.y - cj.y, X2 = ci.z - cj.z;
-                        const float d2 = X0 * X0 + X1 * X1 + X2 * X2;
-                        hit = d2 < g.rc2f;
-                        if (fabsf(d2 - g.rc2f) < g.bandf) {
-                            int dx, dy, dz, kx, ky, kz;
-                            stencil_offset(HALF, T.jst[k], dx, dy, dz);
-                            wrap_axis(cx, dx, g.nc[0], kx);
-                            wrap_axis(cy, dy, g.nc[1], ky);
-                            wrap_axis(cz, dz, g.nc[2], kz);
-                            const double *ri = r64 + 3LL * si, *rj = r64 + 3LL * __float_as_int(cj.w);
-                            const double e0 = __dsub_rn(__dsub_rn(ri[0], rj[0]), (double)kx * g.L[0]);
-                            const double e1 = __dsub_rn(__dsub_rn(ri[1], rj[1]), (double)ky * g.L[1]);
-                            const double e2 = __dsub_rn(__dsub_rn(ri[2], rj[2]), (double)kz * g.L[2]);
-                            hit = __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2)) < g.rc2;
-                        }
+                // squared COM distance of candidate k (huge if k is not a candidate of i)
+                auto dist2 = [&](int k) -> float {
+                    if (k >= nj || k == self_k) return 3.0e38f;
+                    const float4 cj = T.jc[k];
+                    const float X0 = ci.x - cj.x, X1 = ci.y - cj.y, X2 = ci.z - cj.z;
+                    return X0 * X0 + X1 * X1 + X2 * X2;
+                };
+                // the same test in FP64 from the FP64 state (pairs near the cut-off)
+                auto test64 = [&](int k) -> bool {
+                    int dx, dy, dz, kx, ky, kz;
+                    stencil_offset(HALF, T.jst[k], dx, dy, dz);
+                    wrap_axis(cx, dx, g.nc[0], kx);
+                    wrap_axis(cy, dy, g.nc[1], ky);
+                    wrap_axis(cz, dz, g.nc[2], kz);
+                    const double *ri = r64 + 3LL * si, *rj = r64 + 3LL * __float_as_int(T.jc[k].w);
+                    const double e0 = __dsub_rn(__dsub_rn(ri[0], rj[0]), (double)kx * g.L[0]);
+                    const double e1 = __dsub_rn(__dsub_rn(ri[1], rj[1]), (double)ky * g.L[1]);
+                    const double e2 = __dsub_rn(__dsub_rn(ri[2], rj[2]), (double)kz * g.L[2]);
+                    return __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2)) < g.rc2;
+                };
+                // two candidates per lane per round (independent tests), then
+                // the hits are appended in candidate order
+                for (int kb = skip_to; kb < nj; kb += 64) {
+                    const int k0 = kb + lane, k1 = kb + 32 + lane;
+                    const float d0 = dist2(k0), d1 = dist2(k1);
+                    bool h0 = d0 < g.rc2f, h1 = d1 < g.rc2f;
+                    const bool n0 = fabsf(d0 - g.rc2f) < g.bandf, n1 = fabsf(d1 - g.rc2f) < g.bandf;
+                    if (__any_sync(FULLMASK, n0 || n1)) {  // rare: decide in FP64
+                        if (n0) h0 = test64(k0);
+                        if (n1) h1 = test64(k1);
                     }
-                    const unsigned bal = __ballot_sync(FULLMASK, hit);
-                    if (hit) T.queue[qn + __popc(bal & lt_mask)] = tag | k;
-                    qn += __popc(bal);
-                    if (qn >= 32) {
+                    const unsigned b0 = __ballot_sync(FULLMASK, h0), b1 = __ballot_sync(FULLMASK, h1);
+                    if (h0) T.queue[qn + __popc(b0 & lt_mask)] = tag | k0;
+                    qn += __popc(b0);
+                    if (h1) T.queue[qn + __popc(b1 & lt_mask)] = tag | k1;
+                    qn += __popc(b1);
+                    while (qn >= 32) {
                         __syncwarp();
                         chunk(32);
                         __syncwarp();
-                        if (lane < qn - 32) T.queue[lane] = T.queue[32 + lane];
+                        for (int t = lane; t < qn - 32; t += 32) T.queue[t] = T.queue[32 + t];
                         qn -= 32;
                         __syncwarp();
                     }

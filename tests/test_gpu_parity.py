@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle,
 element by element on the same seeded inputs.
 
-Tolerances (FP32 site math, FP64 accumulation; see DESIGN.md):
+Tolerances (FP32 site math, FP64 accumulation):
   * forces and torques: floored relative error
     |F - F_ref| / max(|F_ref|, 0.01 F_rms) with median <= 1e-5, max <= 1e-3;
   * energy and virial: |dU| <= 1e-5 * sum_ij |u_ij| and |dW| <= 1e-5 *
@@ -25,6 +25,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_1408_4599_gb300 import md  # noqa: E402
+from test_oracle_pins import _half_step_temperature  # noqa: E402
 
 LOG = os.environ.get("MD_PARITY_LOG")
 
@@ -212,16 +213,20 @@ def test_nonfinite_input_rejected_on_host():
 
 
 # ----------------------------------------------------------- trajectories
-def _traj_compare(cfg, n_steps, tol):
-    s = md.System(cfg)
+def _traj_compare(cfg, n_steps, tol, T_target=0.0, half=0):
+    s = md.System(cfg, deterministic=1 - half, half_shell=half)
     s.set(cfg["r"], cfg["q"], cfg["v"], cfg["j"])
-    s.step(n_steps, cfg["dt"])
+    s.step(n_steps, cfg["dt"], T_target=T_target)
     r, v, q, j = s.molecules()
     F, tau = s.forces()
     obs = s.observables()
     s.close()
     st = oracle.step(cfg["model"], oracle.setup_from_config(cfg), {k: cfg[k] for k in ("r", "v", "q", "j")},
-                     cfg["dt"], n_steps, use_cells=True)
+                     cfg["dt"], n_steps, use_cells=True, T_target=T_target)
+    if T_target > 0:
+        # the half-step temperature the thermostat set, from the GPU state
+        T_half = _half_step_temperature(cfg["model"], v, q, j)
+        assert T_half == pytest.approx(T_target, rel=1e-6)
     L = np.array(cfg["box"])
     dr = r - st["r"]
     dr -= L * np.rint(dr / L)
@@ -249,6 +254,23 @@ def test_trajectory_4site_10_steps():
     cfg["v"] *= 0.1
     cfg["j"] *= 0.1
     _traj_compare(cfg, 10, 1e-5)
+
+
+@pytest.mark.parametrize("half", [0, 1])
+def test_trajectory_2cljq_nvt(half):
+    """Velocity rescaling (§2 NVT) to a temperature well away from the start."""
+    _traj_compare(mdgen.config_2cljq(n=4000), 20, 1e-5, T_target=1.4, half=half)
+
+
+def test_trajectory_4site_nvt():
+    cfg = mdgen.config_4site(n=2000)
+    cfg["v"] *= 0.1
+    cfg["j"] *= 0.1
+    _traj_compare(cfg, 10, 1e-5, T_target=0.05)
+
+
+def test_trajectory_lj_nvt():
+    _traj_compare(mdgen.config_lj_fluid(n=4096), 50, 1e-5, T_target=0.8)
 
 
 # -------------------------------------------------- full benchmark sizes
