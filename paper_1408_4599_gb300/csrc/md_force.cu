@@ -24,7 +24,7 @@ using namespace mdk;
 namespace {
 
 #ifndef MD_FORCE_MINB
-#define MD_FORCE_MINB 1
+#define MD_FORCE_MINB 4  // 4 blocks of 4 warps: at most 128 registers
 #endif
 
 template <class SIG, bool HALF>

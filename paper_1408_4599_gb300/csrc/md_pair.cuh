@@ -463,8 +463,9 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
     const int cx = (int)(c % g.nc[0]);
     const int cy = (int)((c / g.nc[0]) % g.nc[1]);
     const int cz = (int)(c / ((long long)g.nc[0] * g.nc[1]));
-    // stencil cell of lane t (< NOFF): first slot, count, image offset; all
-    // loaded at once, then broadcast by shuffles while staging
+    // stencil cell of lane t (< NOFF): first slot, count, image offset and
+    // the exclusive prefix of the counts (position in the concatenated
+    // candidate list); loaded at once, then read by shuffles while staging
     int t_j0 = 0, t_cnt = 0;
     float t_ox = 0.f, t_oy = 0.f, t_oz = 0.f;
     if (lane < NOFF) {
@@ -480,6 +481,15 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
         t_oy = dy * g.ellf[1];
         t_oz = dz * g.ellf[2];
     }
+    int t_pre = t_cnt;  // inclusive scan, then exclusive
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULLMASK, t_pre, o);
+        if (lane >= o) t_pre += v;
+    }
+    const int n_cand = __shfl_sync(FULLMASK, t_pre, NOFF - 1);
+    t_pre -= t_cnt;
+    const int self_pre = __shfl_sync(FULLMASK, t_pre, SELF), self_cnt = __shfl_sync(FULLMASK, t_cnt, SELF);
     for (int ig = 0; ig < n_i; ig += IMAX) {
         const int ni = min(IMAX, n_i - ig);
         op.pass_begin(ig, ni, lane);
@@ -502,32 +512,35 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
             }
             op.chunk_end(T, il, valid, lane);
         };
-        int o_cur = 0, o_pos = 0;
-        while (o_cur < NOFF) {
-            int nj = 0, self_lo = 0, self_n = 0, self_base = 0;
-            while (o_cur < NOFF && nj < JCAP) {
-                const int j0 = __shfl_sync(FULLMASK, t_j0, o_cur), cnt = __shfl_sync(FULLMASK, t_cnt, o_cur);
-                const float ox = __shfl_sync(FULLMASK, t_ox, o_cur), oy = __shfl_sync(FULLMASK, t_oy, o_cur),
-                            oz = __shfl_sync(FULLMASK, t_oz, o_cur);
-                const int take = min(cnt - o_pos, JCAP - nj);
-                if (o_cur == SELF) {  // the i-cell: local index self_lo + (k - self_base)
-                    self_lo = o_pos;
-                    self_n = take;
-                    self_base = nj;  // 0 in the half shell (stencil index 0 opens a segment)
+        // segments: consecutive windows of <= JCAP entries of the candidate list
+        for (int seg0 = 0; seg0 < n_cand; seg0 += JCAP) {
+            const int nj = min(JCAP, n_cand - seg0);
+            // every lane stages entries x = seg0 + lane + 32 b; its stencil
+            // cell is the last one whose prefix is <= x (binary search over
+            // the lanes' prefixes); the loads of all rounds are independent
+#pragma unroll 2
+            for (int tb = 0; tb < nj; tb += 32) {  // warp-uniform trip count: the shuffles need every lane
+                const int t = tb + lane;
+                const int x = seg0 + t;
+                int o = 0;
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1) {
+                    const int c2 = o + st;
+                    const int p2 = __shfl_sync(FULLMASK, t_pre, c2 < NOFF ? c2 : 0);
+                    if (c2 < NOFF && p2 <= x) o = c2;
                 }
-                for (int t = lane; t < take; t += 32) {
-                    const int js = j0 + o_pos + t;
+                const int js = __shfl_sync(FULLMASK, t_j0, o) + (x - __shfl_sync(FULLMASK, t_pre, o));
+                const float ox = __shfl_sync(FULLMASK, t_ox, o), oy = __shfl_sync(FULLMASK, t_oy, o),
+                            oz = __shfl_sync(FULLMASK, t_oz, o);
+                if (t < nj) {
                     const float4 cj = com[js];
-                    T.jc[nj + t] = make_float4(cj.x + ox, cj.y + oy, cj.z + oz, __int_as_float(js));
-                    T.jst[nj + t] = (unsigned char)o_cur;
-                }
-                nj += take;
-                o_pos += take;
-                if (o_pos >= cnt) {
-                    o_cur++;
-                    o_pos = 0;
+                    T.jc[t] = make_float4(cj.x + ox, cj.y + oy, cj.z + oz, __int_as_float(js));
+                    T.jst[t] = (unsigned char)o;
                 }
             }
+            // the i-cell's entries in this window: local index self_lo + (k - self_base)
+            const int w_lo = max(self_pre, seg0), w_hi = min(self_pre + self_cnt, seg0 + nj);
+            const int self_n = max(0, w_hi - w_lo), self_lo = w_lo - self_pre, self_base = w_lo - seg0;
             op.seg_begin(T, nj, lane);
             __syncwarp();
             int qn = 0;
