@@ -101,7 +101,7 @@ struct AdjOp {
     }
     __device__ void pass_begin(int, int, int) {}
     __device__ void seg_begin(Tile &, int, int) {}
-    __device__ void chunk_end(Tile &, int, bool, int) {}
+    __device__ void chunk_end(Tile &, int, int, bool, int) {}
     __device__ void seg_end(Tile &, int, int) {}
     __device__ void pass_end(int, int, int, int) {}
     __device__ void count_examined(int n) { nexam += n; }
@@ -119,7 +119,7 @@ struct AdjOp {
         W += sab * w1;
     }
 
-    __device__ void pair(Tile &, const IMol<SIG> &I, int, float X0, float X1, float X2, int js, bool)
+    __device__ void pair(Tile &, const IMol<SIG> &I, int, float X0, float X1, float X2, int js)
     {
         const float4 *gj = A.geo + (long long)js * K;
         float U = 0.f, W = 0.f;

@@ -465,7 +465,7 @@ md_status alloc_molecules(md_system *s, long long n)
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.perm2, nn * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.com, nn * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.geo, nn * (size_t)(d.K > 0 ? d.K : 1) * sizeof(float4));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&d.facc, nn * 6 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.facc, nn * FACC_STRIDE * sizeof(float));
     if (e != cudaSuccess) return cuda_fail(s, e, "allocating molecule buffers");
     s->cap = n;
     d.n = n;

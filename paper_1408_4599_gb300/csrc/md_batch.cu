@@ -384,7 +384,7 @@ BatchArgs batch_args(md_batch *b, bool half_list)
 md_status batch_force(md_batch *b, cudaStream_t st)
 {
     DevState &d = b->d;
-    BCK(cudaMemsetAsync(d.facc, 0, sizeof(float) * 6 * (d.n > 0 ? d.n : 1), st), "zero accumulators");
+    BCK(cudaMemsetAsync(d.facc, 0, sizeof(float) * FACC_STRIDE * (d.n > 0 ? d.n : 1), st), "zero accumulators");
     BCK(cudaMemsetAsync(b->counters, 0, 2 * sizeof(int), st), "zero work queues");
     for (int h = 1; h >= 0; h--) {
         BatchArgs B = batch_args(b, h == 1);
@@ -611,7 +611,7 @@ md_status md_batch_set_molecules(md_batch *b, const int64_t *n_per_sys, const do
             if (e == cudaSuccess) e = cudaMalloc((void **)p, nn * sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc((void **)&d.com, nn * sizeof(float4));
         if (e == cudaSuccess) e = cudaMalloc((void **)&d.geo, nn * (size_t)(d.K > 0 ? d.K : 1) * sizeof(float4));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&d.facc, nn * 6 * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&d.facc, nn * FACC_STRIDE * sizeof(float));
         if (e != cudaSuccess) return bcuda(b, e, "allocating batch molecule buffers");
         b->cap = ntot;
     }

@@ -78,17 +78,18 @@ __global__ void __launch_bounds__(MD_WARPS * 32, MD_FORCE_MINB) k_force(const __
     }
 }
 
-// Half shell: FP32 accumulators (SoA) -> FP64 F, tau; non-finite check.
+// Half shell: FP32 accumulator records -> FP64 F, tau; non-finite check.
 __global__ void k_force_finalize(const float *acc, long long n, double *F, double *tau, int *flags)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
+    const float4 f = reinterpret_cast<const float4 *>(acc)[2 * s], t = reinterpret_cast<const float4 *>(acc)[2 * s + 1];
+    const float fv[3] = {f.x, f.y, f.z}, tv[3] = {t.x, t.y, t.z};
     bool bad = false;
     for (int q = 0; q < 3; q++) {
-        const float f = acc[q * n + s], t = acc[(q + 3) * n + s];
-        bad |= !isfinite(f) || !isfinite(t);
-        F[3 * s + q] = (double)f;
-        tau[3 * s + q] = (double)t;
+        bad |= !isfinite(fv[q]) || !isfinite(tv[q]);
+        F[3 * s + q] = (double)fv[q];
+        tau[3 * s + q] = (double)tv[q];
     }
     if (bad) atomicExch(&flags[FLAG_NONFINITE], 1);
 }
@@ -148,7 +149,7 @@ cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half
     cudaError_t e = cudaMemsetAsync(d.partials, 0, sizeof(double) * P_COUNT * n_blocks, s);
     if (e != cudaSuccess) return e;
     if (half_shell) {
-        e = cudaMemsetAsync(d.facc, 0, sizeof(float) * 6 * (d.n > 0 ? d.n : 1), s);
+        e = cudaMemsetAsync(d.facc, 0, sizeof(float) * FACC_STRIDE * (d.n > 0 ? d.n : 1), s);
         if (e != cudaSuccess) return e;
     }
     return dispatch_sig(m, LaunchForce{A, half_shell, n_blocks, s});

@@ -15,7 +15,7 @@ struct ForceArgs {
     const float4 *geo;
     const double *r;
     double *F, *tau;  // outputs (FP64, storage order)
-    float *acc;       // half shell: 6 x n FP32 accumulators (SoA)
+    float *acc;       // half shell: n x FACC_STRIDE FP32 accumulator records
     long long n;
     double *partials;
     int *flags;
@@ -37,6 +37,7 @@ struct ForceOp {
     int K;
     int ig;
     float pF0, pF1, pF2, pT0, pT1, pT2;            // the lane's pair of the current chunk (i side)
+    float tq0, tq1, tq2;                           // its torque on j (half shell)
     float cU, cW, cX, cY, cZ;                      // pass sums of energy and virial (FP32)
     float sU, kU, sW, kW, sX, kX, sY, kY, sZ, kZ;  // compensated lane totals
     int nmol, nexam;
@@ -61,7 +62,7 @@ struct ForceOp {
                 for (int q = 0; q < 6; q++) TT.x.jacc[q][t] = 0.f;
     }
     __device__ void count_examined(int n) { nexam += n; }
-    __device__ void pair(Tile &TT, const IMol<SIG> &I, int k, float X0, float X1, float X2, int js, bool uniq)
+    __device__ void pair(Tile &, const IMol<SIG> &I, int, float X0, float X1, float X2, int js)
     {
         float Fp[3], tp[3], tq[3], Up;
         mol_pair<SIG, HALF>(m, X0, X1, X2, I, A.geo + (long long)js * K, Fp, tp, tq, Up);
@@ -78,23 +79,37 @@ struct ForceOp {
         cZ += X2 * Fp[2];
         nmol++;
         if (HALF) {
-            // the Newton-3 reaction on j; a j that meets two i's of one chunk
-            // is the rare case that needs shared-memory atomics
-            float *J = &TT.x.jacc[0][0];
-            const float rv[6] = {-Fp[0], -Fp[1], -Fp[2], tq[0], tq[1], tq[2]};
-            if (uniq) {
-#pragma unroll
-                for (int q = 0; q < 6; q++) J[q * JCAP + k] += rv[q];
-            } else {
-#pragma unroll
-                for (int q = 0; q < 6; q++) atomicAdd(J + q * JCAP + k, rv[q]);
-            }
+            tq0 = tq[0];
+            tq1 = tq[1];
+            tq2 = tq[2];
         }
     }
-    // i side of a chunk: a segmented suffix sum over the lanes (the pairs of
-    // one i are contiguous); the first lane of each i adds the i's total.
-    __device__ void chunk_end(Tile &, int il, bool valid, int lane)
+    // End of a chunk.  j side (half shell): the Newton-3 reactions go into the
+    // staged candidates' shared accumulators one i at a time, since a j can
+    // meet two i's of a chunk but only once per i.  i side: a segmented suffix
+    // sum over the lanes; the first lane of each i adds the i's total.
+    __device__ void chunk_end(Tile &TT, int il, int k, bool valid, int lane)
     {
+        const int prev = __shfl_up_sync(FULLMASK, il, 1);
+        const bool head = valid && (lane == 0 || prev != il);
+        if (HALF) {
+            float *J = &TT.x.jacc[0][0];
+            unsigned hm = __ballot_sync(FULLMASK, head);
+            while (hm) {  // warp-uniform
+                const int h = __ffs(hm) - 1;
+                hm &= hm - 1;
+                const int ilh = __shfl_sync(FULLMASK, il, h);  // every lane takes part in the shuffle
+                if (valid && il == ilh) {
+                    J[0 * JCAP + k] -= pF0;
+                    J[1 * JCAP + k] -= pF1;
+                    J[2 * JCAP + k] -= pF2;
+                    J[3 * JCAP + k] += tq0;
+                    J[4 * JCAP + k] += tq1;
+                    J[5 * JCAP + k] += tq2;
+                }
+                __syncwarp();
+            }
+        }
         float v[6] = {pF0, pF1, pF2, pT0, pT1, pT2};
         if (!valid)
 #pragma unroll
@@ -109,8 +124,7 @@ struct ForceOp {
                 if (take) v[q] += o;
             }
         }
-        const int prev = __shfl_up_sync(FULLMASK, il, 1);
-        if (valid && (lane == 0 || prev != il)) {
+        if (head) {
             float *ip = T->x.ipart[il];
 #pragma unroll
             for (int q = 0; q < 6; q++) ip[q] += v[q];
@@ -121,8 +135,9 @@ struct ForceOp {
         if (HALF)
             for (int t = lane; t < nj; t += 32) {
                 const int js = __float_as_int(TT.jc[t].w);
-#pragma unroll
-                for (int q = 0; q < 6; q++) atomicAdd(A.acc + (long long)q * A.n + js, TT.x.jacc[q][t]);
+                float *a = A.acc + (long long)FACC_STRIDE * js;
+                red_add_v4(a, TT.x.jacc[0][t], TT.x.jacc[1][t], TT.x.jacc[2][t], 0.f);
+                red_add_v4(a + 4, TT.x.jacc[3][t], TT.x.jacc[4][t], TT.x.jacc[5][t], 0.f);
             }
     }
     __device__ void pass_end(int s0, int ig_, int ni, int lane)
@@ -131,8 +146,9 @@ struct ForceOp {
             const int si = s0 + ig_ + t;
             const float *ip = T->x.ipart[t];
             if (HALF || A.to_acc) {
-#pragma unroll
-                for (int q = 0; q < 6; q++) atomicAdd(A.acc + (long long)q * A.n + si, ip[q]);
+                float *a = A.acc + (long long)FACC_STRIDE * si;
+                red_add_v4(a, ip[0], ip[1], ip[2], 0.f);
+                red_add_v4(a + 4, ip[3], ip[4], ip[5], 0.f);
             } else {
                 double *Fo = A.F + 3LL * si, *To = A.tau + 3LL * si;
                 Fo[0] = ip[0];

@@ -74,7 +74,7 @@ struct DevState {
     double *kin_partials;           // kinetic partials, 4 per block ([2], [3]: half-step K for the thermostat)
     double *thermo;                 // [0] velocity-rescaling factor of the last step, [1] its T_half
     int *flags;                     // [0] non-finite, [1] overflow, [2] timeout
-    float *facc;                    // 6 x n FP32 force/torque accumulators (half shell)
+    float *facc;                    // n x 8 FP32 accumulators per molecule: F (3), 0, tau (3), 0 (half shell)
 };
 
 // Compiled model of a system (used by the batched replicas, which compile
@@ -86,6 +86,17 @@ struct ModelInfo {
     double lrc_u_coef, lrc_w_coef, rf_self_per_mol;
 };
 void model_info(const md_system *s, ModelInfo *out);
+
+// Accumulator record of one molecule: two 16-byte halves (F, 0) and (tau, 0).
+constexpr int FACC_STRIDE = 8;
+
+// Element-wise atomic add of four floats to a 16-byte aligned address (one
+// vector reduction instead of four scalar ones).
+__device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
 
 // Partial-sum layout of the force kernel (per block).
 enum { P_U = 0, P_W, P_WXX, P_WYY, P_WZZ, P_NMOL, P_NSITE, P_NEXAM, P_COUNT };

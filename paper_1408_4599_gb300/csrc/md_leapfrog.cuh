@@ -68,7 +68,8 @@ __device__ __forceinline__ void quat_rate_f(const float q[4], const float w[3], 
 
 // One step of molecule s in place; cc receives its cell coordinates after
 // the periodic wrap.  ACC32: the forces and torques are read from the FP32
-// Newton-3 accumulators (6 x n, SoA), otherwise from the FP64 arrays.
+// accumulator records (F, 0, tau, 0 per molecule), otherwise from the FP64
+// arrays.
 // Returns true if a non-finite value appeared.
 template <bool ACC32>
 __device__ __forceinline__ bool leapfrog_one(const DevModel &m, const DevState &d, long long s, const LeapArgs &a,
@@ -76,8 +77,14 @@ __device__ __forceinline__ bool leapfrog_one(const DevModel &m, const DevState &
                                              int (&cc)[3])
 {
     bool bad = false;
+    float4 fa = make_float4(0.f, 0.f, 0.f, 0.f), ta = fa;
+    if (ACC32) {
+        fa = reinterpret_cast<const float4 *>(d.facc)[2 * s];
+        ta = reinterpret_cast<const float4 *>(d.facc)[2 * s + 1];
+    }
+    const float fav[3] = {fa.x, fa.y, fa.z}, tav[3] = {ta.x, ta.y, ta.z};
     for (int k = 0; k < 3; k++) {
-        const double F = ACC32 ? (double)d.facc[k * d.n + s] : d.F[3 * s + k];
+        const double F = ACC32 ? (double)fav[k] : d.F[3 * s + k];
         const double v = d.v[3 * s + k] + a.dtm * F;  // Eq. 2
         double r = d.r[3 * s + k] + a.dt * v;         // Eq. 3
         bad |= !isfinite(r);
@@ -99,7 +106,7 @@ __device__ __forceinline__ bool leapfrog_one(const DevModel &m, const DevState &
         for (int k = 0; k < 4; k++) qf[k] = (float)q[k];
         for (int k = 0; k < 3; k++) {
             if (ACC32) {
-                tf[k] = d.facc[(3 + k) * d.n + s];
+                tf[k] = tav[k];
                 t[k] = (double)tf[k];
             } else {
                 t[k] = d.tau[3 * s + k];

@@ -438,12 +438,12 @@ struct GridView {
 //   pass_begin(ig, ni, lane) / pass_end(s0, ig, ni, lane)
 //   seg_begin(T, nj, lane)            after a segment has been staged
 //   seg_end(T, nj, lane)              after all i's of a pass met the segment
-//   pair(T, I, k, X0, X1, X2, js, uniq)
-//                                     the lane's queued pair (i molecule I,
-//                                     staged candidate k, storage slot js);
-//                                     uniq: no other lane of the chunk has k
-//   chunk_end(T, il, valid, lane)     all lanes, after the pairs of a chunk;
+//   pair(T, I, k, X0, X1, X2, js)     the lane's queued pair (i molecule I,
+//                                     staged candidate k, storage slot js)
+//   chunk_end(T, il, k, valid, lane)  all lanes, after the pairs of a chunk;
 //                                     il = the lane's i index in the pass
+//                                     (lanes of one i are contiguous and
+//                                     their k are distinct)
 //   count_examined(n)
 // cell_start holds global slots; c is the cell index inside the grid.
 template <class SIG, bool HALF, class Op, class Extra>
@@ -502,15 +502,13 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
                 il = e >> 16;
                 k = e & 0xffff;
             }
-            bool uniq = true;
-            if (HALF) uniq = __match_any_sync(FULLMASK, k) == (1u << lane);
             if (valid) {
                 IMol<SIG> I;
                 load_i<SIG>(m, com, geo, K, s0 + ig + il, I);
                 const float4 cj = T.jc[k];
-                op.pair(T, I, k, I.c.x - cj.x, I.c.y - cj.y, I.c.z - cj.z, __float_as_int(cj.w), uniq);
+                op.pair(T, I, k, I.c.x - cj.x, I.c.y - cj.y, I.c.z - cj.z, __float_as_int(cj.w));
             }
-            op.chunk_end(T, il, valid, lane);
+            op.chunk_end(T, il, k, valid, lane);
         };
         // segments: consecutive windows of <= JCAP entries of the candidate list
         for (int seg0 = 0; seg0 < n_cand; seg0 += JCAP) {
