@@ -233,10 +233,19 @@ md_status md_batch_set_molecules(md_batch *b, const int64_t *n_per_sys, const do
 /* Forces of every replica at the current configuration.  Asynchronous. */
 md_status md_batch_compute_forces(md_batch *b, void *cuda_stream);
 
-/* n_steps leapfrog steps (NVE) of every replica.  use_graph != 0 captures
+/* n_steps leapfrog steps of every replica (NVE, or NVT for the replicas
+ * given a target by md_batch_set_thermostat).  use_graph != 0 captures
  * pairs of steps into a CUDA graph once (per buffer parity and dt) and
  * replays it; an odd last step runs eagerly.  Asynchronous. */
 md_status md_batch_step(md_batch *b, int32_t n_steps, double dt, int32_t use_graph, void *cuda_stream);
+
+/* Per-replica NVT by velocity rescaling (§2, ensembles), as md_step with
+ * T_target: T_target (host, n_sys; NULL = all NVE) > 0 gives replica k the
+ * target T_target[k], <= 0 leaves it NVE.  The factors are computed on the
+ * device every step (one block per replica) and applied while v and j are
+ * reordered, so captured graphs need no host work.  Errors: MD_ERR_ARG
+ * (non-finite target).  Synchronising. */
+md_status md_batch_set_thermostat(md_batch *b, const double *T_target, void *cuda_stream);
 
 /* Observables of every replica (out: n_sys entries, host).  Synchronising. */
 md_status md_batch_energy_virial(md_batch *b, md_observables *out, void *cuda_stream);

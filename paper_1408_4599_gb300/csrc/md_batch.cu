@@ -63,6 +63,9 @@ struct md_batch {
     int *cellN = nullptr;     // 2 per cell
     double *rep_obs = nullptr;  // 8 per replica
     double *rep_kin = nullptr;  // 2 per replica
+    double *rep_T = nullptr;    // per-replica thermostat target (<= 0: NVE)
+    double *rep_beta = nullptr; // per-replica velocity-rescaling factor of the last step
+    bool nvt = false;           // some replica has a target
     bool has_mol = false, forces_valid = false;
     bool f_in_acc = false;  // the latest forces exist only in the FP32 accumulators
     double dt_last = 0.0, time = 0.0;
@@ -126,7 +129,7 @@ __global__ void k_integrate_b(const RepGrid *G, const int *rep, DevModel m, DevS
     atomicAdd(&d.cell_count[c], 1);
 }
 
-__global__ void k_reorder_pack_b(const RepGrid *G, const int *rep, DevModel m, DevState d)
+__global__ void k_reorder_pack_b(const RepGrid *G, const int *rep, DevModel m, DevState d, const double *beta)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= d.n) return;
@@ -135,9 +138,10 @@ __global__ void k_reorder_pack_b(const RepGrid *G, const int *rep, DevModel m, D
     d.r2[3 * s] = rx;
     d.r2[3 * s + 1] = ry;
     d.r2[3 * s + 2] = rz;
+    const double b = beta ? beta[rep[s]] : 1.0;  // velocity rescaling of the slot's replica
     for (int k = 0; k < 3; k++) {
-        d.v2[3 * s + k] = d.v[3 * o + k];
-        d.j2[3 * s + k] = d.j[3 * o + k];
+        d.v2[3 * s + k] = b * d.v[3 * o + k];
+        d.j2[3 * s + k] = b * d.j[3 * o + k];
     }
     const double qw = d.q[4 * o], qx = d.q[4 * o + 1], qy = d.q[4 * o + 2], qz = d.q[4 * o + 3];
     d.q2[4 * s] = qw;
@@ -306,6 +310,46 @@ __global__ void k_rep_kinetic(const RepGrid *G, int n_sys, long long n, DevModel
     }
 }
 
+// Velocity rescaling per replica (§2 NVT), one block per replica: half-step
+// kinetic temperature (v, j at t + dt/2, q at t + dt; translational part in
+// FP64, rotational per molecule in FP32 with FP64 sums) and the factor
+// sqrt(T_k / T_half), 1 for replicas without a target.
+__global__ void k_rep_thermostat(const RepGrid *G, int n_sys, long long n, DevModel m, DevState d, const double *Tt,
+                                 double *beta)
+{
+    const int k = blockIdx.x;
+    if (k >= n_sys) return;
+    const long long s0 = G[k].mol0, s1 = (k + 1 < n_sys) ? G[k + 1].mol0 : n;
+    __shared__ double sh[32];
+    double e = 0.0;  // 2 K
+    const float Iinv[3] = {(float)m.Iinv[0], (float)m.Iinv[1], (float)m.Iinv[2]};
+    const float Im[3] = {(float)m.I[0], (float)m.I[1], (float)m.I[2]};
+    if (Tt[k] > 0.0)
+        for (long long s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+            const double v0 = d.v[3 * s], v1 = d.v[3 * s + 1], v2 = d.v[3 * s + 2];
+            e += m.mass * (v0 * v0 + v1 * v1 + v2 * v2);
+            if (m.rot_dof > 0) {
+                const float qf[4] = {(float)d.q[4 * s], (float)d.q[4 * s + 1], (float)d.q[4 * s + 2],
+                                     (float)d.q[4 * s + 3]};
+                const float jf[3] = {(float)d.j[3 * s], (float)d.j[3 * s + 1], (float)d.j[3 * s + 2]};
+                float w[3];
+                omega_body_f(qf, jf, Iinv, w);
+                e += (double)(Im[0] * w[0] * w[0] + Im[1] * w[1] * w[1] + Im[2] * w[2] * w[2]);
+            }
+        }
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
+        const double N = (double)(s1 - s0), dof = 3.0 * N - 3.0 + (double)m.rot_dof * N;
+        const double T = dof > 0.0 ? t / dof : 0.0;
+        beta[k] = (Tt[k] > 0.0 && T > 0.0 && isfinite(T)) ? sqrt(Tt[k] / T) : 1.0;
+    }
+}
+
 struct LaunchBatchForce {
     const BatchArgs &B;
     int half, blocks_cap;
@@ -405,7 +449,7 @@ md_status batch_forces_to_f64(md_batch *b, cudaStream_t st)
     return MD_OK;
 }
 
-md_status batch_rebuild(md_batch *b, cudaStream_t st, bool need_cellid)
+md_status batch_rebuild(md_batch *b, cudaStream_t st, bool need_cellid, const double *beta = nullptr)
 {
     DevState &d = b->d;
     if (need_cellid) {
@@ -413,7 +457,7 @@ md_status batch_rebuild(md_batch *b, cudaStream_t st, bool need_cellid)
         if (d.n > 0) k_cellid_b<<<nb256(d.n), 256, 0, st>>>(b->dgrids, b->rep_of_slot, d.r, d.cell, d.cell_count, d.n);
     }
     BCK(launch_sort(b->ncell, d, st), "counting sort");
-    if (d.n > 0) k_reorder_pack_b<<<nb256(d.n), 256, 0, st>>>(b->dgrids, b->rep_of_slot, b->m, d);
+    if (d.n > 0) k_reorder_pack_b<<<nb256(d.n), 256, 0, st>>>(b->dgrids, b->rep_of_slot, b->m, d, beta);
     BCK(cudaGetLastError(), "reorder/pack kernel");
     swap_state(d);
     return MD_OK;
@@ -425,7 +469,11 @@ md_status batch_one_step(md_batch *b, double dt, cudaStream_t st)
     BCK(cudaMemsetAsync(d.cell_count, 0, sizeof(int) * b->ncell, st), "zero counts");
     if (d.n > 0) k_integrate_b<<<nb256(d.n), 256, 0, st>>>(b->dgrids, b->rep_of_slot, b->m, d, leap_args(b->m, dt));
     BCK(cudaGetLastError(), "integrate kernel");
-    md_status ms = batch_rebuild(b, st, false);
+    if (b->nvt) {
+        k_rep_thermostat<<<b->n_sys, 256, 0, st>>>(b->dgrids, b->n_sys, d.n, b->m, d, b->rep_T, b->rep_beta);
+        BCK(cudaGetLastError(), "thermostat kernel");
+    }
+    md_status ms = batch_rebuild(b, st, false, b->nvt ? b->rep_beta : nullptr);
     if (ms != MD_OK) return ms;
     return batch_force(b, st);
 }
@@ -446,13 +494,13 @@ void batch_free(md_batch *b)
     void *ptrs[] = {d.r, d.v, d.q, d.j, d.r2, d.v2, d.q2, d.j2, d.ids, d.ids2, d.F, d.tau, d.cell, d.cell_count,
                     d.cell_start, d.cell_fill, d.perm, d.perm2, d.com, d.geo, d.scan_tmp, d.flags, d.facc,
                     b->dgrids, b->rep_of_slot, b->rep_of_cell, b->work, b->counters, b->cellE, b->cellN,
-                    b->rep_obs, b->rep_kin};
+                    b->rep_obs, b->rep_kin, b->rep_T, b->rep_beta};
     for (void *p : ptrs) cudaFree(p);
     memset(&b->d, 0, sizeof b->d);
     b->dgrids = nullptr;
     b->rep_of_slot = b->rep_of_cell = b->work = b->counters = b->cellN = nullptr;
     b->cellE = nullptr;
-    b->rep_obs = b->rep_kin = nullptr;
+    b->rep_obs = b->rep_kin = b->rep_T = b->rep_beta = nullptr;
     b->cap = 0;
 }
 
@@ -538,6 +586,9 @@ md_status md_batch_create(int32_t n_sys, const double *boxes, double cutoff, con
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->cellN, sizeof(int) * 2 * nc_tot);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->rep_obs, sizeof(double) * 8 * n_sys);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->rep_kin, sizeof(double) * 2 * n_sys);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->rep_T, sizeof(double) * n_sys);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->rep_beta, sizeof(double) * n_sys);
+    if (e == cudaSuccess) e = cudaMemset(b->rep_T, 0, sizeof(double) * n_sys);
     if (e == cudaSuccess) e = cudaMemset(b->cellE, 0, sizeof(float) * 5 * nc_tot);
     if (e == cudaSuccess) e = cudaMemset(b->cellN, 0, sizeof(int) * 2 * nc_tot);
     if (e == cudaSuccess) {
@@ -840,6 +891,28 @@ md_status md_batch_get_forces(md_batch *b, double *F, double *tau, int32_t on_de
 
 // Times the batched force evaluation for each (work-chunk size, grid
 // occupancy) candidate with CUDA events and keeps the fastest.
+md_status md_batch_set_thermostat(md_batch *b, const double *T_target, void *cuda_stream)
+{
+    if (!b) return MD_ERR_ARG;
+    std::vector<double> t(b->n_sys, 0.0);
+    bool any = false;
+    if (T_target)
+        for (int k = 0; k < b->n_sys; k++) {
+            if (!std::isfinite(T_target[k])) {
+                bset_err(b, "md_batch_set_thermostat: non-finite target temperature");
+                return MD_ERR_ARG;
+            }
+            t[k] = T_target[k] > 0.0 ? T_target[k] : 0.0;
+            any = any || t[k] > 0.0;
+        }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    BCK(cudaMemcpyAsync(b->rep_T, t.data(), sizeof(double) * b->n_sys, cudaMemcpyHostToDevice, st), "copy targets");
+    BCK(cudaStreamSynchronize(st), "md_batch_set_thermostat sync");
+    if (any != b->nvt) drop_graphs(b);  // the captured step differs with and without the thermostat
+    b->nvt = any;
+    return MD_OK;
+}
+
 md_status md_batch_tune(md_batch *b, void *cuda_stream, int32_t *best_chunk, int32_t *best_grid_pct, float *best_ms)
 {
     if (!b) return MD_ERR_ARG;

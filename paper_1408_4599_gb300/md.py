@@ -69,7 +69,7 @@ EXPORTS = ("md_create", "md_set_molecules", "md_compute_forces", "md_step", "md_
            "md_destroy", "md_status_str", "md_last_error", "md_n_params", "md_get_params", "md_set_params",
            "md_param_grad", "md_batch_create", "md_batch_set_molecules", "md_batch_compute_forces", "md_batch_step",
            "md_batch_energy_virial", "md_batch_get_molecules", "md_batch_get_forces", "md_batch_tune",
-           "md_batch_destroy", "md_batch_last_error", "md_kinetic_noalloc")
+           "md_batch_destroy", "md_batch_last_error", "md_batch_set_thermostat", "md_kinetic_noalloc")
 
 
 def lib():
@@ -107,12 +107,14 @@ def lib():
         L.md_batch_get_molecules.argtypes = [vp, vp, vp, vp, vp, i32, vp]
         L.md_batch_get_forces.argtypes = [vp, vp, vp, i32, vp]
         L.md_batch_tune.argtypes = [vp, vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_float)]
+        L.md_batch_set_thermostat.argtypes = [vp, dp, vp]
         L.md_batch_destroy.argtypes = [vp]
         L.md_batch_destroy.restype = None
         L.md_batch_last_error.argtypes = [vp]
         L.md_batch_last_error.restype = C.c_char_p
         for name in ("md_batch_create", "md_batch_set_molecules", "md_batch_compute_forces", "md_batch_step",
-                     "md_batch_energy_virial", "md_batch_get_molecules", "md_batch_get_forces", "md_batch_tune"):
+                     "md_batch_energy_virial", "md_batch_get_molecules", "md_batch_get_forces", "md_batch_tune",
+                     "md_batch_set_thermostat"):
             getattr(L, name).restype = C.c_int
         L.md_kinetic_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, C.c_double, dp, C.c_double, vp, vp]
         L.md_kinetic_noalloc.restype = C.c_int
@@ -452,6 +454,16 @@ class Batch:
         F, tau = np.zeros((n, 3)), np.zeros((n, 3))
         _bcheck(lib().md_batch_get_forces(self.h, _ptr(F)[0], _ptr(tau)[0], 0, _stream_ptr(stream)), self.h)
         return F, tau
+
+    def set_thermostat(self, T_target=None, stream=None):
+        """Per-replica NVT targets (sequence of n_sys; <= 0 or None: NVE)."""
+        if T_target is None:
+            _bcheck(lib().md_batch_set_thermostat(self.h, None, _stream_ptr(stream)), self.h)
+            return
+        t = np.ascontiguousarray(np.asarray(T_target, dtype=np.float64))
+        if t.shape != (len(self.cfgs),):
+            raise ValueError("one target per replica")
+        _bcheck(lib().md_batch_set_thermostat(self.h, t.ctypes.data_as(dp), _stream_ptr(stream)), self.h)
 
     def tune(self, stream=None):
         bc, bg, bm = C.c_int32(), C.c_int32(), C.c_float()

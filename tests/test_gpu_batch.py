@@ -137,3 +137,43 @@ def test_batch_argument_errors():
         b.compute_forces()
     assert e.value.code == -3
     b.close()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_nvt_matches_single_systems(use_graph):
+    """Per-replica velocity rescaling (§2 NVT): the batched step with a
+    target per replica (one replica left NVE) equals each replica's own
+    md_step with that target, and each thermostatted replica's half-step
+    temperature equals its target."""
+    from test_oracle_pins import _half_step_temperature
+    cfgs = _replicas(n_rep=5, seed_k=11)
+    targets = [0.8, 1.5, 0.0, 1.1, 2.0]
+    b = md.Batch(cfgs, half_shell=0).set()
+    b.set_thermostat(targets)
+    b.step(6, 0.001, use_graph=use_graph)
+    rb, vb, qb, jb = b.molecules()
+    b.close()
+    for c, T, r, v, q, j in zip(cfgs, targets, _split(rb, cfgs), _split(vb, cfgs), _split(qb, cfgs), _split(jb, cfgs)):
+        s = md.System(c, deterministic=1)
+        s.set(c["r"], c["q"], c["v"], c["j"])
+        s.step(6, 0.001, T_target=T)
+        r1, v1, q1, j1 = s.molecules()
+        s.close()
+        L = np.array(c["box"])
+        dr = r - r1
+        dr -= L * np.rint(dr / L)
+        assert np.abs(dr).max() < 1e-11 and np.abs(v - v1).max() < 1e-9 and np.abs(j - j1).max() < 1e-9
+        if T > 0:
+            assert _half_step_temperature(c["model"], v, q, j) == pytest.approx(T, rel=1e-6)
+
+
+def test_batch_thermostat_argument_errors():
+    cfgs = _replicas(n_rep=2)
+    b = md.Batch(cfgs)
+    with pytest.raises(ValueError):
+        b.set_thermostat([1.0])
+    with pytest.raises(md.MDError) as e:
+        b.set_thermostat([1.0, math.nan])
+    assert e.value.code == -1
+    b.set_thermostat(None)
+    b.close()
