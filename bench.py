@@ -44,6 +44,25 @@ def flops_per_pair():
     return int(re.search(r"#define MD_FLOPS_PAIR_2CLJQ (\d+)", txt).group(1))
 
 
+FORCE_SOURCES = ("md_force.cu", "md_forceop.cuh", "md_internal.cuh", "md_pair.cuh")
+
+
+def force_traffic():
+    """DRAM bytes per launch of the half-shell force kernel from the committed
+    ncu summary, if it was taken from the sources as they are now (else None)."""
+    import hashlib
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "k_force_2cljq_N262144.md")).read()
+        want = re.search(r"source_sha256: ([0-9a-f]{64})", txt).group(1)
+        traffic = int(re.search(r"traffic_bytes_per_launch: (\d+)", txt).group(1))
+    except (OSError, AttributeError):
+        return None
+    h = hashlib.sha256()
+    for f in FORCE_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1408_4599_gb300", "csrc", f), "rb").read())
+    return traffic if h.hexdigest() == want else None
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
 
@@ -247,7 +266,8 @@ def main():
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_force (2CLJQ, " + ("half" if half else "full") + " shell)",
+            "traffic": force_traffic() if half else None,
+            "kernel": "k_force (2CLJQ, " + ("half" if half else "full") + " shell)",
             "flops_per_pair": fpp, "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
             f"{sm_max:.0f} MHz (FP32 FMA)",
             "frac_at_sampled_clock": (achieved / (peak * clk["sm_mhz"] / sm_max)) if clk.get("sm_mhz") else None,

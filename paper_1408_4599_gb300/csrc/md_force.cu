@@ -23,12 +23,15 @@ using namespace mdk;
 
 namespace {
 
-#ifndef MD_FORCE_MINB
-#define MD_FORCE_MINB 4  // 4 blocks of 4 warps: at most 128 registers
-#endif
+// Resident blocks the register budget is sized for: 4 blocks of 4 warps (at
+// most 128 registers) for models of up to 3 merged sites, 3 blocks (168) for
+// the larger compiled signatures, whose site loops spill at 128 registers,
+// and 2 for the run-time signature.
+template <class SIG>
+constexpr int force_min_blocks() { return SIG::DYN ? 2 : (SIG::S <= 3 ? 4 : 3); }
 
 template <class SIG, bool HALF>
-__global__ void __launch_bounds__(MD_WARPS * 32, MD_FORCE_MINB) k_force(const __grid_constant__ ForceArgs A)
+__global__ void __launch_bounds__(MD_WARPS * 32, force_min_blocks<SIG>()) k_force(const __grid_constant__ ForceArgs A)
 {
     using Op = ForceOp<SIG, HALF>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
