@@ -57,8 +57,8 @@ __host__ __device__ constexpr int sig_lj(unsigned R, int a)
 template <class SIG>
 struct AdjLayout;
 
-template <int S_, unsigned R_, bool SG_, unsigned TY_>
-struct AdjLayout<SigStatic<S_, R_, SG_, TY_>> {
+template <int S_, unsigned R_, bool SG_, unsigned TY_, bool LIN_>
+struct AdjLayout<SigStatic<S_, R_, SG_, TY_, LIN_>> {
     static constexpr int NLJ = sig_nlj(R_, S_);
     static constexpr int NE = sig_ne(R_, S_);
     static constexpr int NACC = 4 * NLJ * NLJ + 2 * NE * NE + 2;  // + U, W
@@ -123,14 +123,21 @@ struct AdjOp {
     {
         const float4 *gj = A.geo + (long long)js * K;
         float U = 0.f, W = 0.f;
+        float4 uj = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (SIG::LIN) uj = __ldg(gj);  // the j molecule's axis
 #pragma unroll
         for (int b = 0; b < S; b++) {
             const int rb = SIG::role(b, m);
             if (rb == 0) continue;
-            float4 db = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (!SIG::SINGLE) db = __ldg(gj + b);
-            float4 eb = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (rb & AX_ROLES) eb = __ldg(gj + SIG::s_of(m) + SIG::slot(b, m));
+            float4 db = make_float4(0.f, 0.f, 0.f, 0.f), eb = db;
+            if constexpr (SIG::LIN) {
+                const float z = m.body[b][2], sb = m.axis[b][2];
+                db = make_float4(z * uj.x, z * uj.y, z * uj.z, 0.f);
+                if (rb & AX_ROLES) eb = make_float4(sb * uj.x, sb * uj.y, sb * uj.z, 0.f);
+            } else {
+                if (!SIG::SINGLE) db = __ldg(gj + b);
+                if (rb & AX_ROLES) eb = __ldg(gj + SIG::s_of(m) + SIG::slot(b, m));
+            }
 #pragma unroll
             for (int a = 0; a < S; a++) {
                 const int ra = SIG::role(a, m);

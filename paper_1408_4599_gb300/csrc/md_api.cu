@@ -347,6 +347,13 @@ md_status compile_model(md_system *s, const md_site_types *t, double rc, int lj_
     m.site_pairs_per_mol_pair = s->n_lj * s->n_lj + s->n_el * s->n_el;
     m.single_lj_at_com = (m.S == 1 && m.roles[0] == ROLE_LJ && sites[0].pos[0] == 0.0 && sites[0].pos[1] == 0.0 &&
                           sites[0].pos[2] == 0.0);
+    m.linear = !m.single_lj_at_com;
+    for (int a = 0; a < m.S; a++) {
+        const HSite &h = sites[a];
+        if (h.pos[0] != 0.0 || h.pos[1] != 0.0) m.linear = 0;
+        if (h.has_axis && (h.axis[0] != 0.0 || h.axis[1] != 0.0 || std::fabs(std::fabs(h.axis[2]) - 1.0) > 1e-12))
+            m.linear = 0;
+    }
     m.mass = mass;
     for (int k = 0; k < 3; k++) {
         m.I[k] = In[4 * k];
@@ -610,7 +617,7 @@ md_status md_create(const double box[3], double cutoff, const md_site_types *typ
     g.rc2f = (float)g.rc2;
     g.bandf = (float)(2e-5 * g.rc2);
     s->half_eff = (opt.half_shell && !opt.deterministic && g.nc[0] >= 3 && g.nc[1] >= 3 && g.nc[2] >= 3) ? 1 : 0;
-    s->d.K = s->m.single_lj_at_com ? 0 : s->m.S + s->m.NA;
+    s->d.K = s->m.single_lj_at_com ? 0 : (s->m.linear ? 1 : s->m.S + s->m.NA);
 
     long long fb = (ncell + MD_WARPS - 1) / MD_WARPS;
     s->n_force_blocks = (int)(fb < force_blocks_default() ? fb : force_blocks_default());  // upper bound of the grid

@@ -160,6 +160,10 @@ __global__ void k_reorder_pack_b(const RepGrid *G, const int *rep, DevModel m, D
                         2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
                         2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
     float4 *out = d.geo + s * (long long)d.K;
+    if (m.linear) {  // the molecular axis R(q) z carries every site offset and axis
+        out[0] = make_float4(R[2], R[5], R[8], 0.f);
+        return;
+    }
     for (int a = 0; a < m.S; a++) {
         const float *b = m.body[a];
         out[a] = make_float4(R[0] * b[0] + R[1] * b[1] + R[2] * b[2], R[3] * b[0] + R[4] * b[1] + R[5] * b[2],
@@ -569,7 +573,7 @@ md_status md_batch_create(int32_t n_sys, const double *boxes, double cutoff, con
     }
     b->ncell = nc_tot;
     b->g.ncell = nc_tot;
-    b->d.K = b->m.single_lj_at_com ? 0 : b->m.S + b->m.NA;
+    b->d.K = b->m.single_lj_at_com ? 0 : (b->m.linear ? 1 : b->m.S + b->m.NA);
     DevState &d = b->d;
     cudaError_t e = cudaMalloc((void **)&d.cell_count, sizeof(int) * nc_tot);
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.cell_start, sizeof(int) * (nc_tot + 1));

@@ -207,6 +207,10 @@ __global__ void k_reorder_pack(Grid g, DevModel m, DevState d, const double *bet
                   2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
                   2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};
     float4 *out = d.geo + s * (long long)d.K;
+    if (m.linear) {  // the molecular axis R(q) z carries every site offset and axis
+        out[0] = make_float4(R[2], R[5], R[8], 0.0f);
+        return;
+    }
     for (int a = 0; a < m.S; a++) {
         const float *b = m.body[a];
         out[a] = make_float4(R[0] * b[0] + R[1] * b[1] + R[2] * b[2], R[3] * b[0] + R[4] * b[1] + R[5] * b[2],

@@ -35,6 +35,8 @@ struct DevModel {
     float frf;                      // reaction-field factor / rc^3
     int site_pairs_per_mol_pair;    // n_lj^2 + n_el^2 of the user's entities
     int single_lj_at_com;           // 1: one LJ site at the centre of mass, nothing else
+    int linear;                     // 1: every site on the body z axis, every axis along +-z: the packed
+                                    //    geometry is the space-frame molecular axis alone
     double mass;
     double Iinv[3], I[3];
     int rot_dof;                    // 0, 2 or 3

@@ -52,13 +52,16 @@ constexpr unsigned SIG_4SITE = sigkey(ROLE_LJ, ROLE_LJ | ROLE_CHG, ROLE_LJ | ROL
 
 // Compile-time site-role signature: S sites, 4 role bits per site, and the
 // LJ type of each LJ site (4 bits per site), so that the mixing-table
-// entries are compile-time constant-bank operands.
-template <int S_, unsigned R_, bool SINGLE_ = false, unsigned TY_ = 0>
+// entries are compile-time constant-bank operands.  LIN: a linear molecule
+// (DevModel::linear), whose packed geometry is its space-frame axis u alone;
+// site a sits at body_z(a) u and its axis is axis_z(a) u.
+template <int S_, unsigned R_, bool SINGLE_ = false, unsigned TY_ = 0, bool LIN_ = false>
 struct SigStatic {
     static constexpr int S = S_;
     static constexpr bool DYN = false;
     static constexpr bool SINGLE = SINGLE_;
-    static constexpr int K = S_ + sig_na(R_, S_);
+    static constexpr bool LIN = LIN_;
+    static constexpr int K = LIN_ ? 1 : S_ + sig_na(R_, S_);
     __device__ __forceinline__ static constexpr int role(int a, const DevModel &) { return sig_role(R_, a); }
     __device__ __forceinline__ static constexpr int slot(int a, const DevModel &) { return sig_slot(R_, a); }
     __device__ __forceinline__ static constexpr int type(int a, const DevModel &) { return sig_role(TY_, a); }
@@ -71,6 +74,7 @@ struct SigDyn {
     static constexpr int S = MD_MAX_SITES;
     static constexpr bool DYN = true;
     static constexpr bool SINGLE = false;
+    static constexpr bool LIN = false;
     __device__ __forceinline__ static int role(int a, const DevModel &m) { return a < m.S ? m.roles[a] : 0; }
     __device__ __forceinline__ static int slot(int a, const DevModel &m) { return m.axis_slot[a]; }
     __device__ __forceinline__ static int type(int a, const DevModel &m) { return m.lj_type[a]; }
@@ -90,9 +94,13 @@ __host__ auto dispatch_sig(const DevModel &m, F &&f)
         if (m.roles[a] & ROLE_LJ) ty |= (unsigned)m.lj_type[a] << (4 * a);
     }
     if (m.single_lj_at_com && ty == 0) return f.template operator()<SigStatic<1, ROLE_LJ, true>>();
-    if (m.S == 2 && key == SIG_2CLJ && ty == 0) return f.template operator()<SigStatic<2, SIG_2CLJ>>();
-    if (m.S == 3 && key == SIG_2CLJQ && ty == 0) return f.template operator()<SigStatic<3, SIG_2CLJQ>>();
-    if (m.S == 3 && key == SIG_2CLJDQ && ty == 0) return f.template operator()<SigStatic<3, SIG_2CLJDQ>>();
+    // the two-centre models are compiled for the linear geometry only
+    if (m.linear && m.S == 2 && key == SIG_2CLJ && ty == 0)
+        return f.template operator()<SigStatic<2, SIG_2CLJ, false, 0, true>>();
+    if (m.linear && m.S == 3 && key == SIG_2CLJQ && ty == 0)
+        return f.template operator()<SigStatic<3, SIG_2CLJQ, false, 0, true>>();
+    if (m.linear && m.S == 3 && key == SIG_2CLJDQ && ty == 0)
+        return f.template operator()<SigStatic<3, SIG_2CLJDQ, false, 0, true>>();
     if (m.S == 5 && key == SIG_4SITE && ty == TY_4SITE)
         return f.template operator()<SigStatic<5, SIG_4SITE, false, TY_4SITE>>();
     return f.template operator()<SigDyn>();
@@ -274,6 +282,19 @@ __device__ __forceinline__ void load_i(const DevModel &m, const float4 *com, con
 {
     I.slot = si;
     I.c = com[si];
+    if constexpr (SIG::LIN) {
+        const float4 u = geo[(long long)si * K];
+#pragma unroll
+        for (int a = 0; a < SIG::S; a++) {
+            const float z = m.body[a][2], sa = m.axis[a][2];
+            I.d[a][0] = z * u.x;
+            I.d[a][1] = z * u.y;
+            I.d[a][2] = z * u.z;
+            I.e[a] = (SIG::role(a, m) & AX_ROLES) ? make_float4(sa * u.x, sa * u.y, sa * u.z, 0.f)
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < SIG::S; a++) {
         I.d[a][0] = I.d[a][1] = I.d[a][2] = 0.f;
@@ -321,13 +342,21 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
         fa[0][1] = fr * X1;
         fa[0][2] = fr * X2;
     } else {
+        float4 uj = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (SIG::LIN) uj = __ldg(gj);  // the j molecule's axis
 #pragma unroll
         for (int b = 0; b < S; b++) {
             const int rb = SIG::role(b, m);
             if (rb == 0) continue;
-            const float4 db = __ldg(gj + b);
-            float4 eb = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (rb & AX_ROLES) eb = __ldg(gj + SIG::s_of(m) + SIG::slot(b, m));
+            float4 db, eb = make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (SIG::LIN) {
+                const float z = m.body[b][2], sb = m.axis[b][2];
+                db = make_float4(z * uj.x, z * uj.y, z * uj.z, 0.f);
+                if (rb & AX_ROLES) eb = make_float4(sb * uj.x, sb * uj.y, sb * uj.z, 0.f);
+            } else {
+                db = __ldg(gj + b);
+                if (rb & AX_ROLES) eb = __ldg(gj + SIG::s_of(m) + SIG::slot(b, m));
+            }
 #pragma unroll
             for (int a = 0; a < S; a++) {
                 const int ra = SIG::role(a, m);

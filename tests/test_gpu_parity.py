@@ -289,3 +289,48 @@ def test_full_size_slab_parity():
     Fo, to, oo = oracle_eval(cfg)
     F, tau, obs = gpu_eval(cfg, deterministic=0, half=1)
     check_parity("slab-4194304/half1", cfg, F, tau, obs, Fo, to, oo)
+
+
+# ------------------------------------------------- NVE drift over 1000 steps
+def _energy_series(run_chunk, n_chunks):
+    E = []
+    for _ in range(n_chunks):
+        E.append(run_chunk())
+    return np.array(E)
+
+
+def test_nve_energy_drift_1000_steps():
+    """LJTS fluid (N = 4096, T = 0.95, dt = 0.002) for 1000 leapfrog steps:
+    the total energy of the GPU path drifts no more than the FP64 oracle's
+    own drift plus three times the oracle's energy fluctuation (linear fit
+    over the 1000 steps; the trajectories themselves diverge, as chaotic
+    trajectories do, once rounding differs)."""
+    cfg = mdgen.config_lj_fluid(n=4096)
+    dt, every, n_chunks = cfg["dt"], 10, 100
+    s = md.System(cfg, deterministic=1)
+    s.set(cfg["r"], cfg["q"], cfg["v"], cfg["j"])
+
+    def gpu_chunk():
+        s.step(every, dt)
+        o = s.observables()
+        return o["U_pot"] + o["K_trans"] + o["K_rot"]
+
+    Eg = _energy_series(gpu_chunk, n_chunks)
+    s.close()
+    setup = oracle.setup_from_config(cfg)
+    st = {k: cfg[k] for k in ("r", "v", "q", "j")}
+    Eo = []
+    for _ in range(n_chunks):
+        st = oracle.step(cfg["model"], setup, st, dt, every, use_cells=True)
+        kt, kr = oracle.kinetic(cfg["model"], dt, st["v"], st["q"], st["j"], st["F"], st["tau"])
+        Eo.append(st["obs"]["U"] + kt + kr)
+    Eo = np.array(Eo)
+    t = np.arange(1, n_chunks + 1) * every * dt
+    fit_g, fit_o = np.polyfit(t, Eg, 1), np.polyfit(t, Eo, 1)
+    span = t[-1] - t[0]
+    drift_g, drift_o = fit_g[0] * span, fit_o[0] * span
+    rms_o = float(np.std(Eo - np.polyval(fit_o, t)))
+    _log(case="nve-drift/lj-4096", steps=n_chunks * every, drift_gpu=float(drift_g), drift_oracle=float(drift_o),
+         rms_fluct_oracle=rms_o, drift_gpu_per_step_per_mol=float(fit_g[0] * dt / 4096),
+         drift_oracle_per_step_per_mol=float(fit_o[0] * dt / 4096))
+    assert abs(drift_g) <= abs(drift_o) + 3.0 * rms_o + 1e-9 * abs(Eo).max()
