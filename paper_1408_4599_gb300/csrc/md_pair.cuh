@@ -438,7 +438,11 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 #define MD_JCAP 256
 #endif
 constexpr int JCAP = MD_JCAP;  // staged candidates per segment (a multiple of 32)
-constexpr int QCAP = 96;    // hit queue (31 waiting + 2 x 32 new)
+#ifndef MD_TEST_UNROLL
+#define MD_TEST_UNROLL 8
+#endif
+constexpr int NTEST = MD_TEST_UNROLL;   // candidates per lane per test round
+constexpr int QCAP = 32 * (NTEST + 1);  // hit queue (31 waiting + NTEST x 32 new)
 
 // Per-warp staging area; Extra is the pair operation's own shared state.
 template <class Extra>
@@ -598,22 +602,28 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
                     const double e2 = __dsub_rn(__dsub_rn(ri[2], rj[2]), (double)kz * g.L[2]);
                     return __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2)) < g.rc2;
                 };
-                // two candidates per lane per round (independent tests), then
-                // the hits are appended in candidate order
-                for (int kb = skip_to; kb < nj; kb += 64) {
-                    const int k0 = kb + lane, k1 = kb + 32 + lane;
-                    const float d0 = dist2(k0), d1 = dist2(k1);
-                    bool h0 = d0 < g.rc2f, h1 = d1 < g.rc2f;
-                    const bool n0 = fabsf(d0 - g.rc2f) < g.bandf, n1 = fabsf(d1 - g.rc2f) < g.bandf;
-                    if (__any_sync(FULLMASK, n0 || n1)) {  // rare: decide in FP64
-                        if (n0) h0 = test64(k0);
-                        if (n1) h1 = test64(k1);
+                // NTEST candidates per lane per round (independent tests),
+                // then the hits are appended in candidate order
+                for (int kb = skip_to; kb < nj; kb += 32 * NTEST) {
+                    bool h[NTEST], near[NTEST], any_near = false;
+#pragma unroll
+                    for (int u = 0; u < NTEST; u++) {
+                        const float d2 = dist2(kb + 32 * u + lane);
+                        h[u] = d2 < g.rc2f;
+                        near[u] = fabsf(d2 - g.rc2f) < g.bandf;
+                        any_near |= near[u];
                     }
-                    const unsigned b0 = __ballot_sync(FULLMASK, h0), b1 = __ballot_sync(FULLMASK, h1);
-                    if (h0) T.queue[qn + __popc(b0 & lt_mask)] = tag | k0;
-                    qn += __popc(b0);
-                    if (h1) T.queue[qn + __popc(b1 & lt_mask)] = tag | k1;
-                    qn += __popc(b1);
+                    if (__any_sync(FULLMASK, any_near)) {  // rare: decide in FP64
+#pragma unroll
+                        for (int u = 0; u < NTEST; u++)
+                            if (near[u]) h[u] = test64(kb + 32 * u + lane);
+                    }
+#pragma unroll
+                    for (int u = 0; u < NTEST; u++) {
+                        const unsigned bal = __ballot_sync(FULLMASK, h[u]);
+                        if (h[u]) T.queue[qn + __popc(bal & lt_mask)] = tag | (kb + 32 * u + lane);
+                        qn += __popc(bal);
+                    }
                     while (qn >= 32) {
                         __syncwarp();
                         chunk(32);
