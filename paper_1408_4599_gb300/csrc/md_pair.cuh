@@ -487,9 +487,6 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
 {
     constexpr int IMAX = Op::IMAX;
     static_assert(IMAX <= 32 && JCAP <= 65536, "queue entry packs (i << 16) | k");
-    const int s0 = cell_start[g.cell0 + c];
-    const int n_i = cell_start[g.cell0 + c + 1] - s0;
-    if (n_i == 0) return;
     const unsigned lt_mask = (1u << lane) - 1u;
     constexpr int NOFF = HALF ? 14 : 27;
     constexpr int SELF = HALF ? 0 : 13;  // stencil index of the cell itself
@@ -523,6 +520,9 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
     const int n_cand = __shfl_sync(FULLMASK, t_pre, NOFF - 1);
     t_pre -= t_cnt;
     const int self_pre = __shfl_sync(FULLMASK, t_pre, SELF), self_cnt = __shfl_sync(FULLMASK, t_cnt, SELF);
+    // the i-cell is the stencil's own entry (no separate load round)
+    const int s0 = __shfl_sync(FULLMASK, t_j0, SELF), n_i = self_cnt;
+    if (n_i == 0) return;
     for (int ig = 0; ig < n_i; ig += IMAX) {
         const int ni = min(IMAX, n_i - ig);
         op.pass_begin(ig, ni, lane);
@@ -549,7 +549,7 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
             // every lane stages entries x = seg0 + lane + 32 b; its stencil
             // cell is the last one whose prefix is <= x (binary search over
             // the lanes' prefixes); the loads of all rounds are independent
-#pragma unroll 2
+#pragma unroll 4
             for (int tb = 0; tb < nj; tb += 32) {  // warp-uniform trip count: the shuffles need every lane
                 const int t = tb + lane;
                 const int x = seg0 + t;
