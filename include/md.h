@@ -140,8 +140,11 @@ md_status md_create(const double box[3], double cutoff, const md_site_types *typ
  * comp_id may be NULL (all component 0).  r (n x 3), q (n x 4) required;
  * v, j may be NULL (zero).  Positions are wrapped into [0, L); quaternions
  * are renormalised.  The step counter restarts.  Asynchronous for device
- * input; host input is copied before return.  Errors: MD_ERR_ARG (NULL
- * r/q, n < 0, non-finite input), MD_ERR_OOM. */
+ * input; host input is copied (and validated on the device) before return.
+ * Errors: MD_ERR_ARG (NULL r/q, n < 0; for host input also a non-finite
+ * value or a zero quaternion, after which no molecules are set),
+ * MD_ERR_OOM; invalid device input is reported as MD_ERR_NONFINITE by the
+ * next synchronising call. */
 md_status md_set_molecules(md_system *sys, int64_t n, const int32_t *comp_id, const double *r, const double *v,
                            const double *q, const double *j, int32_t on_device, void *cuda_stream);
 

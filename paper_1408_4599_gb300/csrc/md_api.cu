@@ -509,6 +509,10 @@ md_status check_flags(md_system *s)
         set_err(s, "a bounded device wait gave up");
         return MD_ERR_TIMEOUT;
     }
+    if (h[FLAG_INPUT]) {
+        set_err(s, "md_set_molecules (device input): non-finite r, v or j, or a zero or non-finite quaternion");
+        return MD_ERR_NONFINITE;
+    }
     return MD_OK;
 }
 
@@ -673,21 +677,8 @@ md_status md_set_molecules(md_system *s, int64_t n, const int32_t *comp_id, cons
                 return MD_ERR_ARG;
             }
     }
-    if (!on_device) {
-        for (int64_t i = 0; i < n; i++) {
-            if (!finite3(r + 3 * i) || !finite3(q + 4 * i) || !std::isfinite(q[4 * i + 3]) ||
-                (v && !finite3(v + 3 * i)) || (j && !finite3(j + 3 * i))) {
-                set_err(s, "md_set_molecules: non-finite input for molecule %lld", (long long)i);
-                return MD_ERR_ARG;
-            }
-            double nq = q[4 * i] * q[4 * i] + q[4 * i + 1] * q[4 * i + 1] + q[4 * i + 2] * q[4 * i + 2] +
-                        q[4 * i + 3] * q[4 * i + 3];
-            if (!(nq > 0.0)) {
-                set_err(s, "md_set_molecules: zero quaternion for molecule %lld", (long long)i);
-                return MD_ERR_ARG;
-            }
-        }
-    }
+    // values are validated on the device by the preparation kernel (one
+    // pass over the copied state instead of a host scan of the input)
     md_status ms = alloc_molecules(s, n);
     if (ms != MD_OK) return ms;
     DevState &d = s->d;
@@ -703,6 +694,7 @@ md_status md_set_molecules(md_system *s, int64_t n, const int32_t *comp_id, cons
         CK(cudaMemsetAsync(d.F, 0, b3, st), "zero F");
         CK(cudaMemsetAsync(d.tau, 0, b3, st), "zero tau");
     }
+    CK(cudaMemsetAsync(d.flags + FLAG_INPUT, 0, sizeof(int), st), "clear input flag");
     CK(launch_prepare_input(s->g, d, st), "input preparation kernel");
     s->has_mol = true;
     s->binned = false;
@@ -714,7 +706,17 @@ md_status md_set_molecules(md_system *s, int64_t n, const int32_t *comp_id, cons
     s->last_stream = st;
     ms = do_rebuild(s, st, true);
     if (ms != MD_OK) return ms;
-    if (!on_device) CK(cudaStreamSynchronize(st), "md_set_molecules sync");
+    if (!on_device) {
+        CK(cudaStreamSynchronize(st), "md_set_molecules sync");
+        int bad = 0;
+        CK(cudaMemcpy(&bad, d.flags + FLAG_INPUT, sizeof bad, cudaMemcpyDeviceToHost), "reading the input flag");
+        if (bad) {
+            CK(cudaMemset(d.flags + FLAG_INPUT, 0, sizeof(int)), "clear input flag");
+            s->has_mol = false;
+            set_err(s, "md_set_molecules: non-finite r, v or j, or a zero or non-finite quaternion");
+            return MD_ERR_ARG;
+        }
+    }
     return MD_OK;
 }
 

@@ -277,6 +277,8 @@ __global__ void k_rep_kinetic(const RepGrid *G, int n_sys, long long n, DevModel
     __shared__ double sh[2][32];
     double kt = 0.0, kr = 0.0;
     const double im = 1.0 / m.mass;
+    const float Iinv[3] = {(float)m.Iinv[0], (float)m.Iinv[1], (float)m.Iinv[2]};
+    const float Im[3] = {(float)m.I[0], (float)m.I[1], (float)m.I[2]};
     for (long long s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
         double v2 = 0.0;
         for (int q = 0; q < 3; q++) {
@@ -285,16 +287,9 @@ __global__ void k_rep_kinetic(const RepGrid *G, int n_sys, long long n, DevModel
         }
         kt += 0.5 * m.mass * v2;
         if (m.rot_dof > 0) {
-            const double qw = d.q[4 * s], qx = d.q[4 * s + 1], qy = d.q[4 * s + 2], qz = d.q[4 * s + 3];
-            double jt[3];
-            for (int q = 0; q < 3; q++) jt[q] = d.j[3 * s + q] + dt_half * d.tau[3 * s + q];
-            const double R00 = 1 - 2 * (qy * qy + qz * qz), R01 = 2 * (qx * qy - qw * qz), R02 = 2 * (qx * qz + qw * qy);
-            const double R10 = 2 * (qx * qy + qw * qz), R11 = 1 - 2 * (qx * qx + qz * qz), R12 = 2 * (qy * qz - qw * qx);
-            const double R20 = 2 * (qx * qz - qw * qy), R21 = 2 * (qy * qz + qw * qx), R22 = 1 - 2 * (qx * qx + qy * qy);
-            const double w0 = m.Iinv[0] * (R00 * jt[0] + R10 * jt[1] + R20 * jt[2]);
-            const double w1 = m.Iinv[1] * (R01 * jt[0] + R11 * jt[1] + R21 * jt[2]);
-            const double w2 = m.Iinv[2] * (R02 * jt[0] + R12 * jt[1] + R22 * jt[2]);
-            kr += 0.5 * (m.I[0] * w0 * w0 + m.I[1] * w1 * w1 + m.I[2] * w2 * w2);
+            const double jt[3] = {d.j[3 * s] + dt_half * d.tau[3 * s], d.j[3 * s + 1] + dt_half * d.tau[3 * s + 1],
+                                  d.j[3 * s + 2] + dt_half * d.tau[3 * s + 2]};
+            kr += 0.5 * (double)kin_rot2(d.q + 4 * s, jt, Iinv, Im);
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -333,12 +328,8 @@ __global__ void k_rep_thermostat(const RepGrid *G, int n_sys, long long n, DevMo
             const double v0 = d.v[3 * s], v1 = d.v[3 * s + 1], v2 = d.v[3 * s + 2];
             e += m.mass * (v0 * v0 + v1 * v1 + v2 * v2);
             if (m.rot_dof > 0) {
-                const float qf[4] = {(float)d.q[4 * s], (float)d.q[4 * s + 1], (float)d.q[4 * s + 2],
-                                     (float)d.q[4 * s + 3]};
-                const float jf[3] = {(float)d.j[3 * s], (float)d.j[3 * s + 1], (float)d.j[3 * s + 2]};
-                float w[3];
-                omega_body_f(qf, jf, Iinv, w);
-                e += (double)(Im[0] * w[0] * w[0] + Im[1] * w[1] * w[1] + Im[2] * w[2] * w[2]);
+                const double jh[3] = {d.j[3 * s], d.j[3 * s + 1], d.j[3 * s + 2]};
+                e += (double)kin_rot2(d.q + 4 * s, jh, Iinv, Im);
             }
         }
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);

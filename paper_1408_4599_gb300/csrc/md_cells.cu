@@ -17,12 +17,14 @@ constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
-// Wrap positions into [0, L) and renormalise quaternions (input hygiene).
-__global__ void k_prepare(Grid g, double *r, double *q, long long n, int *flags)
+// Wrap positions into [0, L) and renormalise quaternions (input hygiene);
+// flags[FLAG_INPUT] marks a non-finite r, v, j or a zero / non-finite q.
+__global__ void k_prepare(Grid g, double *r, double *q, const double *v, const double *j, long long n, int *flags)
 {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     bool bad = false;
+    for (int k = 0; k < 3; k++) bad |= !isfinite(v[3 * s + k]) || !isfinite(j[3 * s + k]);
     for (int k = 0; k < 3; k++) {
         double x = r[3 * s + k];
         bad |= !isfinite(x);
@@ -39,7 +41,7 @@ __global__ void k_prepare(Grid g, double *r, double *q, long long n, int *flags)
     q[4 * s + 1] = a * inv;
     q[4 * s + 2] = b * inv;
     q[4 * s + 3] = c * inv;
-    if (bad) atomicExch(&flags[FLAG_NONFINITE], 1);
+    if (bad) atomicExch(&flags[FLAG_INPUT], 1);
 }
 
 __global__ void k_iota(int *ids, long long n)
@@ -242,7 +244,7 @@ int scan_blocks(long long ncell) { return (int)((ncell + SCAN_TILE - 1) / SCAN_T
 cudaError_t launch_prepare_input(const Grid &g, DevState &d, cudaStream_t s)
 {
     if (d.n == 0) return cudaSuccess;
-    k_prepare<<<nblk(d.n, 256), 256, 0, s>>>(g, d.r, d.q, d.n, d.flags);
+    k_prepare<<<nblk(d.n, 256), 256, 0, s>>>(g, d.r, d.q, d.v, d.j, d.n, d.flags);
     k_iota<<<nblk(d.n, 256), 256, 0, s>>>(d.ids, d.n);
     return cudaGetLastError();
 }

@@ -10,18 +10,6 @@ using namespace mdk;
 
 namespace {
 
-// w_body = I^-1 A(q) j, A = R(q)^T (space -> body)
-__device__ __forceinline__ void omega_body(const double q[4], const double j[3], const double Iinv[3], double w[3])
-{
-    const double qw = q[0], qx = q[1], qy = q[2], qz = q[3];
-    const double R00 = 1 - 2 * (qy * qy + qz * qz), R01 = 2 * (qx * qy - qw * qz), R02 = 2 * (qx * qz + qw * qy);
-    const double R10 = 2 * (qx * qy + qw * qz), R11 = 1 - 2 * (qx * qx + qz * qz), R12 = 2 * (qy * qz - qw * qx);
-    const double R20 = 2 * (qx * qz - qw * qy), R21 = 2 * (qy * qz + qw * qx), R22 = 1 - 2 * (qx * qx + qy * qy);
-    w[0] = Iinv[0] * (R00 * j[0] + R10 * j[1] + R20 * j[2]);
-    w[1] = Iinv[1] * (R01 * j[0] + R11 * j[1] + R21 * j[2]);
-    w[2] = Iinv[2] * (R02 * j[0] + R12 * j[1] + R22 * j[2]);
-}
-
 // One leapfrog step per molecule (storage order), then the cell id and
 // histogram for the rebuild that follows.
 template <bool ACC32>
@@ -37,12 +25,16 @@ __global__ void k_integrate(Grid g, DevModel m, DevState d, LeapArgs a)
 }
 
 // Kinetic energies at integer time: v(t) = v + dt/2 F/m, j(t) = j + dt/2 tau.
+// K_trans in FP64; K_rot per molecule in FP32 (w = I^-1 A(q) j(t) from the
+// rounded q and j(t), ~1e-7 relative) with FP64 sums.
 // Block partials: [0] K_trans, [1] K_rot.
 __global__ void k_kinetic(DevModel m, DevState d, double dt_half)
 {
     __shared__ double sh[2][32];
     double kt = 0.0, kr = 0.0;
     const double im = 1.0 / m.mass;
+    const float Iinv[3] = {(float)m.Iinv[0], (float)m.Iinv[1], (float)m.Iinv[2]};
+    const float Im[3] = {(float)m.I[0], (float)m.I[1], (float)m.I[2]};
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < d.n; s += (long long)gridDim.x * blockDim.x) {
         double v2 = 0.0;
         for (int k = 0; k < 3; k++) {
@@ -51,11 +43,9 @@ __global__ void k_kinetic(DevModel m, DevState d, double dt_half)
         }
         kt += 0.5 * m.mass * v2;
         if (m.rot_dof > 0) {
-            const double q[4] = {d.q[4 * s], d.q[4 * s + 1], d.q[4 * s + 2], d.q[4 * s + 3]};
-            double jt[3], w[3];
-            for (int k = 0; k < 3; k++) jt[k] = d.j[3 * s + k] + dt_half * d.tau[3 * s + k];
-            omega_body(q, jt, m.Iinv, w);
-            kr += 0.5 * (m.I[0] * w[0] * w[0] + m.I[1] * w[1] * w[1] + m.I[2] * w[2] * w[2]);
+            const double jt[3] = {d.j[3 * s] + dt_half * d.tau[3 * s], d.j[3 * s + 1] + dt_half * d.tau[3 * s + 1],
+                                  d.j[3 * s + 2] + dt_half * d.tau[3 * s + 2]};
+            kr += 0.5 * (double)kin_rot2(d.q + 4 * s, jt, Iinv, Im);
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -90,11 +80,8 @@ __global__ void k_kinetic_half(DevModel m, DevState d)
         const double v0 = d.v[3 * s], v1 = d.v[3 * s + 1], v2 = d.v[3 * s + 2];
         kt += v0 * v0 + v1 * v1 + v2 * v2;
         if (m.rot_dof > 0) {
-            const float qf[4] = {(float)d.q[4 * s], (float)d.q[4 * s + 1], (float)d.q[4 * s + 2], (float)d.q[4 * s + 3]};
-            const float jf[3] = {(float)d.j[3 * s], (float)d.j[3 * s + 1], (float)d.j[3 * s + 2]};
-            float w[3];
-            omega_body_f(qf, jf, Iinv, w);
-            kr += (double)(Im[0] * w[0] * w[0] + Im[1] * w[1] * w[1] + Im[2] * w[2] * w[2]);
+            const double jh[3] = {d.j[3 * s], d.j[3 * s + 1], d.j[3 * s + 2]};
+            kr += (double)kin_rot2(d.q + 4 * s, jh, Iinv, Im);
         }
     }
     for (int o = 16; o > 0; o >>= 1) {

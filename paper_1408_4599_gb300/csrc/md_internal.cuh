@@ -103,7 +103,7 @@ __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float 
 // Partial-sum layout of the force kernel (per block).
 enum { P_U = 0, P_W, P_WXX, P_WYY, P_WZZ, P_NMOL, P_NSITE, P_NEXAM, P_COUNT };
 
-enum { FLAG_NONFINITE = 0, FLAG_OVERFLOW = 1, FLAG_TIMEOUT = 2 };
+enum { FLAG_NONFINITE = 0, FLAG_OVERFLOW = 1, FLAG_TIMEOUT = 2, FLAG_INPUT = 3 };
 
 // ------------------------------------------------------------- launchers
 // (all return cudaGetLastError() of the launch)

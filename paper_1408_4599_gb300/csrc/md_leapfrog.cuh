@@ -66,6 +66,19 @@ __device__ __forceinline__ void quat_rate_f(const float q[4], const float w[3], 
     qd[3] = 0.5f * (q[0] * w[2] + q[1] * w[1] - q[2] * w[0]);
 }
 
+// Twice the rotational kinetic energy of one molecule, w.I w with
+// w = I^-1 A(q) j, in FP32 from the FP64 q and j (every kinetic-energy
+// kernel uses this one expression, so their per-molecule values agree).
+__device__ __forceinline__ float kin_rot2(const double *q, const double (&j)[3], const float (&Iinv)[3],
+                                          const float (&Im)[3])
+{
+    const float qf[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
+    const float jf[3] = {(float)j[0], (float)j[1], (float)j[2]};
+    float w[3];
+    omega_body_f(qf, jf, Iinv, w);
+    return Im[0] * w[0] * w[0] + Im[1] * w[1] * w[1] + Im[2] * w[2] * w[2];
+}
+
 // One step of molecule s in place; cc receives its cell coordinates after
 // the periodic wrap.  ACC32: the forces and torques are read from the FP32
 // accumulator records (F, 0, tau, 0 per molecule), otherwise from the FP64

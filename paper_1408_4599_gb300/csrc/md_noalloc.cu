@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "../../include/md.h"
+#include "md_leapfrog.cuh"
 
 namespace {
 
@@ -32,17 +33,6 @@ static __device__ __align__(256) double g_kin_scratch[NA_MAX_BLOCKS * 2];
 
 std::mutex g_mu;
 double *g_scratch_ptr[NA_MAX_DEVICES] = {nullptr};
-
-__device__ __forceinline__ void omega_body_na(const double *q, const double *jt, const double *Iinv, double *w)
-{
-    const double qw = q[0], qx = q[1], qy = q[2], qz = q[3];
-    const double R00 = 1 - 2 * (qy * qy + qz * qz), R01 = 2 * (qx * qy - qw * qz), R02 = 2 * (qx * qz + qw * qy);
-    const double R10 = 2 * (qx * qy + qw * qz), R11 = 1 - 2 * (qx * qx + qz * qz), R12 = 2 * (qy * qz - qw * qx);
-    const double R20 = 2 * (qx * qz - qw * qy), R21 = 2 * (qy * qz + qw * qx), R22 = 1 - 2 * (qx * qx + qy * qy);
-    w[0] = Iinv[0] * (R00 * jt[0] + R10 * jt[1] + R20 * jt[2]);
-    w[1] = Iinv[1] * (R01 * jt[0] + R11 * jt[1] + R21 * jt[2]);
-    w[2] = Iinv[2] * (R02 * jt[0] + R12 * jt[1] + R22 * jt[2]);
-}
 
 struct KinArgs {
     long long n;
@@ -69,9 +59,9 @@ __global__ void __launch_bounds__(NA_THREADS) k_kin_partial(KinArgs a)
             jt[k] = a.j[3 * s + k] + a.dt_half * a.tau[3 * s + k];
         }
         kt += 0.5 * a.mass * v2;
-        double w[3];
-        omega_body_na(a.q + 4 * s, jt, a.Iinv, w);
-        kr += 0.5 * (a.I[0] * w[0] * w[0] + a.I[1] * w[1] * w[1] + a.I[2] * w[2] * w[2]);
+        const float Iinv[3] = {(float)a.Iinv[0], (float)a.Iinv[1], (float)a.Iinv[2]};
+        const float Im[3] = {(float)a.I[0], (float)a.I[1], (float)a.I[2]};
+        kr += 0.5 * (double)mdk::kin_rot2(a.q + 4 * s, jt, Iinv, Im);
     }
     for (int o = 16; o > 0; o >>= 1) {
         kt += __shfl_xor_sync(0xffffffffu, kt, o);
