@@ -92,6 +92,10 @@ CASES = {
     "2cljdq-dilute-700": lambda: mdgen.config_replica(5, 700, 0.05, 0.9),
     "4site-6000": lambda: mdgen.config_4site(n=6000),
     "slab-60000": lambda: mdgen.config_slab(n=60000),
+    # dense cells: > 32 molecules per cell (several i passes per cell) and
+    # > 256 stencil candidates (several staged windows per pass)
+    "lj-dense-cells-12000": lambda: mdgen.config_lj_fluid(n=12000, rho=0.9, rc=4.0),
+    "2cljq-dense-cells-8000": lambda: mdgen.config_2cljq(n=8000, rho=0.6, rc=5.0),
 }
 
 
