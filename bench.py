@@ -115,6 +115,19 @@ class ClockSampler:
         return res
 
 
+def whole_job(units, t_ms, world, device):
+    """Units summed over all ranks and the step time maximised over ranks
+    (the whole-job throughput of independent per-rank replicas)."""
+    import torch
+    tot = torch.tensor(units, dtype=torch.float64, device=device)
+    tmax = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(tot)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    return [float(x) for x in tot.tolist()], float(tmax.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -251,14 +264,10 @@ def main():
     n_mol = cfg["r"].shape[0]
 
     # whole job: units of all ranks / max time over ranks
-    tot = torch.tensor([site_pairs, mol_pairs, n_mol * args.steps], dtype=torch.float64, device=dev)
-    tmax = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(tot)
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-    t_s = float(tmax.item()) / 1e3
-    value = float(tot[0].item()) / t_s
-    mol_updates = float(tot[2].item()) / t_s
+    tot, t_max_ms = whole_job([site_pairs, mol_pairs, n_mol * args.steps], t_ms, world, dev)
+    t_s = t_max_ms / 1e3
+    value = tot[0] / t_s
+    mol_updates = tot[2] / t_s
 
     # roofline of the dominant kernel (force): counted FP32 FLOPs per launch
     fk = kt["force"]
