@@ -15,19 +15,23 @@
  * test of an examined candidate (MD_FLOPS_EXAMINED) is overhead and is not
  * counted either (§3: only ~16% of the examined pairs interact).
  *
- * Building blocks:
- *   lever arm X + d_a, once per site of i ..................... 3
- *   LJ-LJ site pair: x = (X + d_a) - d_b 3, r^2 5, rcp 1, s^2 1,
- *     s^6 2, F/r 5, energy 5, site force 3, sum into site a 3 . 28  (1 MUFU)
- *   quadrupole-quadrupole site pair: x 3, r^2 5, rsqrt 1, unit
- *     vector 3, p_a p_b cos_ab 15, law 38, strength 6, energy 1,
- *     radial coefficient 5, axial coefficients 2, force 18,
- *     e_a x e_b 9, orientation torque on i 21, sum into a 3 ... 130 (1 MUFU)
+ * Building blocks (2CLJQ is compiled as a linear molecule with its
+ * quadrupole at the centre of mass: the packed geometry is the molecular
+ * axis u, site offsets are z_a u):
+ *   site offsets z_a u of the 2 LJ sites of i and of j ............ 12
+ *   quadrupole axes of i and j .................................... 6
+ *   lever arm X + z_a u, LJ sites of i ............................. 6
+ *   LJ-LJ site pair: x = (X + z_a u_i) - z_b u_j 3, r^2 5, rcp 1,
+ *     s^2 1, s^6 2, F/r 5, energy 5, site force 3, sum into a 3 .... 28  (1 MUFU)
+ *   quadrupole-quadrupole pair (both at the COM: x = X): r^2 5,
+ *     rsqrt 1, unit vector 3, p_a p_b cos_ab 15, law 38, strength
+ *     6, energy 1, radial coefficient 5, axial coefficients 2, force
+ *     18, e_a x e_b 9, orientation torque on i 21, sum into a 3 .... 127 (1 MUFU)
  *   per molecule pair: total force 3 per site of i, lever-arm
- *     torque 12 per site of i, torque on j from the angular-
- *     momentum balance tau_j = -tau_i - X x F 12, accumulation
- *     of F and tau on i 6, energy 1, virial (trace and
- *     diagonal) 9, Newton-3 reaction on j 6.
+ *     torque u x (sum_a z_a f_a) 24, torque on j from the angular-
+ *     momentum balance tau_j = -tau_i - X x F 12, accumulation of F
+ *     and tau on i 6, energy 1, virial (trace and diagonal) 9,
+ *     Newton-3 reaction on j 6.
  */
 #ifndef MD_FLOPS_H
 #define MD_FLOPS_H
@@ -39,7 +43,7 @@
 #define MD_MUFU_PAIR_LJ1 1
 
 /* 2CLJQ: 2 LJ sites + 1 linear quadrupole at the centre of mass:
- * 3 x 3 + 4 x 28 + 130 + 3 x 3 + 3 x 12 + 12 + 6 + 1 + 9 + 6 = 330 */
+ * 12 + 6 + 6 + 4 x 28 + 127 + 3 x 3 + 24 + 12 + 6 + 1 + 9 + 6 = 330 */
 #define MD_FLOPS_PAIR_2CLJQ 330
 #define MD_MUFU_PAIR_2CLJQ 5
 

@@ -57,8 +57,8 @@ __host__ __device__ constexpr int sig_lj(unsigned R, int a)
 template <class SIG>
 struct AdjLayout;
 
-template <int S_, unsigned R_, bool SG_, unsigned TY_, bool LIN_>
-struct AdjLayout<SigStatic<S_, R_, SG_, TY_, LIN_>> {
+template <int S_, unsigned R_, bool SG_, unsigned TY_, bool LIN_, unsigned COM_>
+struct AdjLayout<SigStatic<S_, R_, SG_, TY_, LIN_, COM_>> {
     static constexpr int NLJ = sig_nlj(R_, S_);
     static constexpr int NE = sig_ne(R_, S_);
     static constexpr int NACC = 4 * NLJ * NLJ + 2 * NE * NE + 2;  // + U, W

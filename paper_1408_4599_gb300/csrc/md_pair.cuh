@@ -55,12 +55,14 @@ constexpr unsigned SIG_4SITE = sigkey(ROLE_LJ, ROLE_LJ | ROLE_CHG, ROLE_LJ | ROL
 // entries are compile-time constant-bank operands.  LIN: a linear molecule
 // (DevModel::linear), whose packed geometry is its space-frame axis u alone;
 // site a sits at body_z(a) u and its axis is axis_z(a) u.
-template <int S_, unsigned R_, bool SINGLE_ = false, unsigned TY_ = 0, bool LIN_ = false>
+template <int S_, unsigned R_, bool SINGLE_ = false, unsigned TY_ = 0, bool LIN_ = false, unsigned COM_ = 0>
 struct SigStatic {
     static constexpr int S = S_;
     static constexpr bool DYN = false;
     static constexpr bool SINGLE = SINGLE_;
     static constexpr bool LIN = LIN_;
+    // bit a: site a sits at the centre of mass (linear signatures)
+    __host__ __device__ static constexpr bool at_com(int a) { return ((COM_ >> a) & 1u) != 0; }
     static constexpr int K = LIN_ ? 1 : S_ + sig_na(R_, S_);
     __device__ __forceinline__ static constexpr int role(int a, const DevModel &) { return sig_role(R_, a); }
     __device__ __forceinline__ static constexpr int slot(int a, const DevModel &) { return sig_slot(R_, a); }
@@ -75,6 +77,7 @@ struct SigDyn {
     static constexpr bool DYN = true;
     static constexpr bool SINGLE = false;
     static constexpr bool LIN = false;
+    __host__ __device__ static constexpr bool at_com(int) { return false; }
     __device__ __forceinline__ static int role(int a, const DevModel &m) { return a < m.S ? m.roles[a] : 0; }
     __device__ __forceinline__ static int slot(int a, const DevModel &m) { return m.axis_slot[a]; }
     __device__ __forceinline__ static int type(int a, const DevModel &m) { return m.lj_type[a]; }
@@ -97,10 +100,11 @@ __host__ auto dispatch_sig(const DevModel &m, F &&f)
     // the two-centre models are compiled for the linear geometry only
     if (m.linear && m.S == 2 && key == SIG_2CLJ && ty == 0)
         return f.template operator()<SigStatic<2, SIG_2CLJ, false, 0, true>>();
-    if (m.linear && m.S == 3 && key == SIG_2CLJQ && ty == 0)
-        return f.template operator()<SigStatic<3, SIG_2CLJQ, false, 0, true>>();
-    if (m.linear && m.S == 3 && key == SIG_2CLJDQ && ty == 0)
-        return f.template operator()<SigStatic<3, SIG_2CLJDQ, false, 0, true>>();
+    // (their multipole site compiled at the centre of mass)
+    if (m.linear && m.S == 3 && key == SIG_2CLJQ && ty == 0 && m.body[2][2] == 0.f)
+        return f.template operator()<SigStatic<3, SIG_2CLJQ, false, 0, true, 4u>>();
+    if (m.linear && m.S == 3 && key == SIG_2CLJDQ && ty == 0 && m.body[2][2] == 0.f)
+        return f.template operator()<SigStatic<3, SIG_2CLJDQ, false, 0, true, 4u>>();
     if (m.S == 5 && key == SIG_4SITE && ty == TY_4SITE)
         return f.template operator()<SigStatic<5, SIG_4SITE, false, TY_4SITE>>();
     return f.template operator()<SigDyn>();
@@ -273,6 +277,7 @@ struct IMol {
     float4 c;                 // centre of mass (cell-centre frame)
     float d[SIG::S][3];       // space-frame site offsets
     float4 e[SIG::S];         // space-frame axes
+    float4 e_axis;            // linear molecules: the molecular axis u
     int slot;
 };
 
@@ -284,6 +289,7 @@ __device__ __forceinline__ void load_i(const DevModel &m, const float4 *com, con
     I.c = com[si];
     if constexpr (SIG::LIN) {
         const float4 u = geo[(long long)si * K];
+        I.e_axis = u;
 #pragma unroll
         for (int a = 0; a < SIG::S; a++) {
             const float z = m.body[a][2], sa = m.axis[a][2];
@@ -325,9 +331,15 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
 #pragma unroll
     for (int a = 0; a < S; a++) {
         fa[a][0] = fa[a][1] = fa[a][2] = 0.f;
-        xa[a][0] = X0 + I.d[a][0];
-        xa[a][1] = X1 + I.d[a][1];
-        xa[a][2] = X2 + I.d[a][2];
+        if (SIG::at_com(a)) {  // zero offset: no add (x + 0 is not folded under IEEE rules)
+            xa[a][0] = X0;
+            xa[a][1] = X1;
+            xa[a][2] = X2;
+        } else {
+            xa[a][0] = X0 + I.d[a][0];
+            xa[a][1] = X1 + I.d[a][1];
+            xa[a][2] = X2 + I.d[a][2];
+        }
     }
     float ti[3] = {0.f, 0.f, 0.f}, tdummy[3];
     float U = 0.f;
@@ -351,7 +363,7 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
             float4 db, eb = make_float4(0.f, 0.f, 0.f, 0.f);
             if constexpr (SIG::LIN) {
                 const float z = m.body[b][2], sb = m.axis[b][2];
-                db = make_float4(z * uj.x, z * uj.y, z * uj.z, 0.f);
+                db = SIG::at_com(b) ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(z * uj.x, z * uj.y, z * uj.z, 0.f);
                 if (rb & AX_ROLES) eb = make_float4(sb * uj.x, sb * uj.y, sb * uj.z, 0.f);
             } else {
                 db = __ldg(gj + b);
@@ -363,9 +375,10 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
                 const bool lj = (ra & ROLE_LJ) && (rb & ROLE_LJ);
                 const bool el = (ra & EL_ROLES) && (rb & EL_ROLES);
                 if (!lj && !el) continue;
-                const float x = xa[a][0] - db.x;
-                const float y = xa[a][1] - db.y;
-                const float z = xa[a][2] - db.z;
+                const bool zb = SIG::LIN && SIG::at_com(b);
+                const float x = zb ? xa[a][0] : xa[a][0] - db.x;
+                const float y = zb ? xa[a][1] : xa[a][1] - db.y;
+                const float z = zb ? xa[a][2] : xa[a][2] - db.z;
                 const float r2 = x * x + y * y + z * z;
                 float fx = 0.f, fy = 0.f, fz = 0.f;
                 float ir = 0.f, ir2;
@@ -396,15 +409,36 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
         }
     }
     float F0 = 0.f, F1 = 0.f, F2 = 0.f;
+    if constexpr (SIG::LIN) {
+        // lever arms z_a u: sum_a z_a u x f_a = u x (sum_a z_a f_a)
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
 #pragma unroll
-    for (int a = 0; a < S; a++) {
-        F0 += fa[a][0];
-        F1 += fa[a][1];
-        F2 += fa[a][2];
-        if (!SIG::SINGLE) {
-            ti[0] += I.d[a][1] * fa[a][2] - I.d[a][2] * fa[a][1];
-            ti[1] += I.d[a][2] * fa[a][0] - I.d[a][0] * fa[a][2];
-            ti[2] += I.d[a][0] * fa[a][1] - I.d[a][1] * fa[a][0];
+        for (int a = 0; a < S; a++) {
+            F0 += fa[a][0];
+            F1 += fa[a][1];
+            F2 += fa[a][2];
+            if (!SIG::at_com(a)) {
+                const float z = m.body[a][2];
+                g0 += z * fa[a][0];
+                g1 += z * fa[a][1];
+                g2 += z * fa[a][2];
+            }
+        }
+        const float4 u = I.e_axis;
+        ti[0] += u.y * g2 - u.z * g1;
+        ti[1] += u.z * g0 - u.x * g2;
+        ti[2] += u.x * g1 - u.y * g0;
+    } else {
+#pragma unroll
+        for (int a = 0; a < S; a++) {
+            F0 += fa[a][0];
+            F1 += fa[a][1];
+            F2 += fa[a][2];
+            if (!SIG::SINGLE) {
+                ti[0] += I.d[a][1] * fa[a][2] - I.d[a][2] * fa[a][1];
+                ti[1] += I.d[a][2] * fa[a][0] - I.d[a][0] * fa[a][2];
+                ti[2] += I.d[a][0] * fa[a][1] - I.d[a][1] * fa[a][0];
+            }
         }
     }
     Fo[0] = F0;
