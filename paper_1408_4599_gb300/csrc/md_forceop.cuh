@@ -31,6 +31,7 @@ struct ForceExtra {
 template <class SIG, bool HALF>
 struct ForceOp {
     static constexpr int IMAX = 32;
+    static constexpr int NQ = SIG::SINGLE ? 3 : 6;  // accumulated values per molecule: F, and tau unless single-site
     using Tile = WarpTile<ForceExtra<HALF>>;
     const DevModel &m;
     const ForceArgs &A;
@@ -59,7 +60,7 @@ struct ForceOp {
         if (HALF)
             for (int t = lane; t < nj; t += 32)
 #pragma unroll
-                for (int q = 0; q < 6; q++) TT.x.jacc[q][t] = 0.f;
+                for (int q = 0; q < NQ; q++) TT.x.jacc[q][t] = 0.f;
     }
     __device__ void count_examined(int n) { nexam += n; }
     __device__ void pair(Tile &, const IMol<SIG> &I, int, float X0, float X1, float X2, int js)
@@ -103,9 +104,11 @@ struct ForceOp {
                     J[0 * JCAP + k] -= pF0;
                     J[1 * JCAP + k] -= pF1;
                     J[2 * JCAP + k] -= pF2;
-                    J[3 * JCAP + k] += tq0;
-                    J[4 * JCAP + k] += tq1;
-                    J[5 * JCAP + k] += tq2;
+                    if (NQ == 6) {
+                        J[3 * JCAP + k] += tq0;
+                        J[4 * JCAP + k] += tq1;
+                        J[5 * JCAP + k] += tq2;
+                    }
                 }
                 __syncwarp();
             }
@@ -119,7 +122,7 @@ struct ForceOp {
             const int ol = __shfl_down_sync(FULLMASK, il, off);
             const bool take = lane + off < 32 && ol == il;
 #pragma unroll
-            for (int q = 0; q < 6; q++) {
+            for (int q = 0; q < NQ; q++) {
                 const float o = __shfl_down_sync(FULLMASK, v[q], off);
                 if (take) v[q] += o;
             }
@@ -127,7 +130,7 @@ struct ForceOp {
         if (head) {
             float *ip = T->x.ipart[il];
 #pragma unroll
-            for (int q = 0; q < 6; q++) ip[q] += v[q];
+            for (int q = 0; q < NQ; q++) ip[q] += v[q];
         }
     }
     __device__ void seg_end(Tile &TT, int nj, int lane)
@@ -137,7 +140,7 @@ struct ForceOp {
                 const int js = __float_as_int(TT.jc[t].w);
                 float *a = A.acc + (long long)FACC_STRIDE * js;
                 red_add_v4(a, TT.x.jacc[0][t], TT.x.jacc[1][t], TT.x.jacc[2][t], 0.f);
-                red_add_v4(a + 4, TT.x.jacc[3][t], TT.x.jacc[4][t], TT.x.jacc[5][t], 0.f);
+                if (NQ == 6) red_add_v4(a + 4, TT.x.jacc[3][t], TT.x.jacc[4][t], TT.x.jacc[5][t], 0.f);
             }
     }
     __device__ void pass_end(int s0, int ig_, int ni, int lane)
@@ -148,17 +151,18 @@ struct ForceOp {
             if (HALF || A.to_acc) {
                 float *a = A.acc + (long long)FACC_STRIDE * si;
                 red_add_v4(a, ip[0], ip[1], ip[2], 0.f);
-                red_add_v4(a + 4, ip[3], ip[4], ip[5], 0.f);
+                if (NQ == 6) red_add_v4(a + 4, ip[3], ip[4], ip[5], 0.f);
             } else {
                 double *Fo = A.F + 3LL * si, *To = A.tau + 3LL * si;
+                const float t0 = NQ == 6 ? ip[3] : 0.f, t1 = NQ == 6 ? ip[4] : 0.f, t2 = NQ == 6 ? ip[5] : 0.f;
                 Fo[0] = ip[0];
                 Fo[1] = ip[1];
                 Fo[2] = ip[2];
-                To[0] = ip[3];
-                To[1] = ip[4];
-                To[2] = ip[5];
-                if (!(isfinite(ip[0]) && isfinite(ip[1]) && isfinite(ip[2]) && isfinite(ip[3]) && isfinite(ip[4]) &&
-                      isfinite(ip[5])))
+                To[0] = t0;
+                To[1] = t1;
+                To[2] = t2;
+                if (!(isfinite(ip[0]) && isfinite(ip[1]) && isfinite(ip[2]) && isfinite(t0) && isfinite(t1) &&
+                      isfinite(t2)))
                     atomicExch(&A.flags[FLAG_NONFINITE], 1);
             }
         }

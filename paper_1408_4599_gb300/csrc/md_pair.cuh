@@ -618,7 +618,7 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
                 const int tag = (il - ig) << 16;
                 // squared COM distance of candidate k (huge if k is not a candidate of i)
                 auto dist2 = [&](int k) -> float {
-                    if (k >= nj || k == self_k) return 3.0e38f;
+                    if (k >= nj || (!HALF && k == self_k)) return 3.0e38f;
                     const float4 cj = T.jc[k];
                     const float X0 = ci.x - cj.x, X1 = ci.y - cj.y, X2 = ci.z - cj.z;
                     return X0 * X0 + X1 * X1 + X2 * X2;
