@@ -184,8 +184,14 @@ def cpu_baseline(seconds_budget=20.0):
         if time.perf_counter() - t0 > seconds_budget / 2 or n >= 8:
             break
     dt = time.perf_counter() - t0
+    # the same evaluation on one thread (one full-size evaluation)
+    t1 = time.perf_counter()
+    _, _, o1 = oracle.forces(cfg["model"], s, cfg["r"], cfg["q"], use_cells=True, n_threads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": pairs / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} full-size oracle force evaluations (linked cells, N=262144, all host cores)"}
+            "sample": f"{n} full-size oracle force evaluations (linked cells, N=262144, all host cores)",
+            "one_thread": {"value": o1["n_site_pairs"] / dt1, "unit": UNIT, "cores": 1,
+                           "sample": "1 full-size oracle force evaluation on one thread"}}
 
 
 def main():
