@@ -28,7 +28,9 @@ LOG = os.environ.get("MD_PARITY_LOG")
 
 
 def _ensemble(name):
-    if name == "4site":
+    if name == "4site-50000":  # the full-size configuration, two of its configurations
+        cfgs = [mdgen.config_4site(cfg=c) for c in range(2)]
+    elif name == "4site":
         cfgs = [mdgen.config_4site(n=3000, cfg=c) for c in range(3)]
     elif name == "2cljdq-rf":
         cfgs = [mdgen.config_replica(c, 2000, 0.6, 1.0) for c in range(3)]
@@ -46,7 +48,7 @@ def _close(d, d_ref, d_abs, rel=1e-5):
     return np.abs(d - d_ref) <= rel * d_abs + 1e-12 * np.abs(d_ref)
 
 
-@pytest.mark.parametrize("name", ["4site", "2cljdq-rf", "2cljq", "ljts"])
+@pytest.mark.parametrize("name", ["4site", "2cljdq-rf", "2cljq", "ljts", "4site-50000"])
 def test_param_grad_matches_oracle(name):
     cfg, r_all, q_all = _ensemble(name)
     s = oracle.setup_from_config(cfg)

@@ -177,3 +177,25 @@ def test_batch_thermostat_argument_errors():
     assert e.value.code == -1
     b.set_thermostat(None)
     b.close()
+
+
+def test_full_size_batch_sampled_parity():
+    """The batched workload at full size (512 replicas, 2.61 M molecules,
+    half shell where a replica has >= 3 cells per axis): forces of every
+    replica in one launch, eight seeded replicas checked in full against
+    the oracle."""
+    specs = mdgen.replica_specs(512)
+    cfgs = [mdgen.config_replica(k, n, min(rho, n / 216.0), T) for k, (n, rho, T) in enumerate(specs)]
+    b = md.Batch(cfgs, half_shell=1).set()
+    b.tune()
+    b.compute_forces()
+    F, tau = b.forces()
+    obs = b.observables()
+    b.close()
+    Fs, ts = _split(F, cfgs), _split(tau, cfgs)
+    for k in sorted(np.random.default_rng(1408_0499).choice(len(cfgs), 8, replace=False)):
+        c = cfgs[k]
+        s = oracle.setup_from_config(c)
+        Fo, to, oo = oracle.forces(c["model"], s, c["r"], c["q"], use_cells=True)
+        ncs = [int(math.floor(L / (c["rc"] * (1 + 1e-9)))) for L in c["box"]]
+        check_parity(f"batch512/{c['name']}", c, Fs[k], ts[k], obs[k], Fo, to, oo, exact_examined=min(ncs) >= 3)
