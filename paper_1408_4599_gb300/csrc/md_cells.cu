@@ -189,11 +189,11 @@ __global__ void k_reorder_pack(Grid g, DevModel m, DevState d, const double *bet
         d.v2[3 * s + k] = b * d.v[3 * o + k];
         d.j2[3 * s + k] = b * d.j[3 * o + k];
     }
-    double qw = d.q[4 * o], qx = d.q[4 * o + 1], qy = d.q[4 * o + 2], qz = d.q[4 * o + 3];
-    d.q2[4 * s] = qw;
-    d.q2[4 * s + 1] = qx;
-    d.q2[4 * s + 2] = qy;
-    d.q2[4 * s + 3] = qz;
+    // quaternion records are 32-byte aligned: two 16-byte moves
+    const double2 q01 = reinterpret_cast<const double2 *>(d.q)[2 * o], q23 = reinterpret_cast<const double2 *>(d.q)[2 * o + 1];
+    reinterpret_cast<double2 *>(d.q2)[2 * s] = q01;
+    reinterpret_cast<double2 *>(d.q2)[2 * s + 1] = q23;
+    const double qw = q01.x, qx = q01.y, qy = q23.x, qz = q23.y;
     d.ids2[s] = d.ids[o];
     int c = d.cell[o];
     int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);

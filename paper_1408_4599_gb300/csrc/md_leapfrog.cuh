@@ -101,9 +101,7 @@ __device__ __forceinline__ bool leapfrog_one(const DevModel &m, const DevState &
         const double v = d.v[3 * s + k] + a.dtm * F;  // Eq. 2
         double r = d.r[3 * s + k] + a.dt * v;         // Eq. 3
         bad |= !isfinite(r);
-        if (r < 0.0) r += L[k];
-        else if (r >= L[k]) r -= L[k];
-        if (!(r >= 0.0 && r < L[k])) {  // moved more than a box length: general wrap
+        if (!(r >= 0.0 && r < L[k])) {  // crossed a face (rare): periodic wrap
             r -= L[k] * floor(r / L[k]);
             if (r >= L[k]) r -= L[k];
             if (r < 0.0) r = 0.0;
