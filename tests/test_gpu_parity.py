@@ -338,3 +338,49 @@ def test_nve_energy_drift_1000_steps():
          rms_fluct_oracle=rms_o, drift_gpu_per_step_per_mol=float(fit_g[0] * dt / 4096),
          drift_oracle_per_step_per_mol=float(fit_o[0] * dt / 4096))
     assert abs(drift_g) <= abs(drift_o) + 3.0 * rms_o + 1e-9 * abs(Eo).max()
+
+
+# ------------------------------------- models outside the compiled signatures
+def _triangle_model():
+    """Three LJ centres (two types) on an equilateral triangle about the
+    centre of mass, each carrying a charge (net zero), plus a point dipole
+    at the centre of mass along z: merged roles LJ|q, LJ|q, LJ|q, mu -- no
+    compiled signature, so the run-time-signature kernels run."""
+    r = 0.45
+    pts = [(r, 0.0, 0.0), (-0.5 * r, 0.5 * math.sqrt(3.0) * r, 0.0), (-0.5 * r, -0.5 * math.sqrt(3.0) * r, 0.0)]
+    return {"lj_types": {"eps": [1.0, 0.7], "sigma": [1.0, 0.85]}, "xi": None, "eta": None,
+            "lj": [{"pos": pts[0], "type": 0, "mass": 1.0 / 3.0},
+                   {"pos": pts[1], "type": 1, "mass": 1.0 / 3.0},
+                   {"pos": pts[2], "type": 1, "mass": 1.0 / 3.0}],
+            "charges": [{"pos": pts[0], "q": 0.5}, {"pos": pts[1], "q": -0.25}, {"pos": pts[2], "q": -0.25}],
+            "dipoles": [{"pos": (0.0, 0.0, 0.0), "axis": (0.0, 0.0, 1.0), "mu": 0.8}],
+            "quads": []}
+
+
+def _triangle_config(n=3000, rho=0.45, T=1.1, seed=77):
+    rng = np.random.default_rng(seed)
+    model = _triangle_model()
+    L = (n / rho) ** (1.0 / 3.0)
+    box = (L, L, L)
+    pos = mdgen.fcc_subset(n, box, rng, jitter=0.05)
+    q = mdgen.random_quaternions(n, rng)
+    q = mdgen.resolve_site_overlaps(model, pos, q, box, rng, d_min=0.6)
+    v = mdgen.mb_velocities(n, T, mdgen.model_mass(model), rng)
+    j = mdgen.angular_momenta(q, mdgen.model_principal_moments(model), T, rng)
+    return {"name": f"triangle-qmu-N{n}", "model": model, "box": box, "rc": 3.0, "lj_shift": 0, "lj_lrc": 1,
+            "eps_rf": 8.0, "dt": 0.001, "T": T, "r": np.ascontiguousarray(np.mod(pos, box)), "v": v, "q": q, "j": j}
+
+
+@pytest.mark.parametrize("half", [0, 1])
+def test_runtime_signature_model_parity(half):
+    cfg = _triangle_config()
+    Fo, to, oo = oracle_eval(cfg)
+    F, tau, obs = gpu_eval(cfg, deterministic=1 - half, half=half)
+    check_parity(f"{cfg['name']}/half{half}", cfg, F, tau, obs, Fo, to, oo)
+
+
+def test_runtime_signature_model_trajectory():
+    cfg = _triangle_config(n=2000, rho=0.3)
+    cfg["v"] *= 0.3
+    cfg["j"] *= 0.3
+    _traj_compare(cfg, 10, 1e-5)
