@@ -100,8 +100,10 @@ __device__ __forceinline__ bool leapfrog_one(const DevModel &m, const DevState &
         const double F = ACC32 ? (double)fav[k] : d.F[3 * s + k];
         const double v = d.v[3 * s + k] + a.dtm * F;  // Eq. 2
         double r = d.r[3 * s + k] + a.dt * v;         // Eq. 3
-        bad |= !isfinite(r);
-        if (!(r >= 0.0 && r < L[k])) {  // crossed a face (rare): periodic wrap
+        // 0 <= r < L as one unsigned compare of the bit patterns (IEEE order
+        // of non-negative doubles; negative values and NaN compare above)
+        if ((unsigned long long)__double_as_longlong(r) >= (unsigned long long)__double_as_longlong(L[k])) {
+            bad |= !isfinite(r);  // crossed a face (rare): periodic wrap
             r -= L[k] * floor(r / L[k]);
             if (r >= L[k]) r -= L[k];
             if (r < 0.0) r = 0.0;
