@@ -6,17 +6,17 @@
 // GB300 design (CUDA cores -- this is not a dense contraction):
 //   * traversal of md_pair.cuh: one warp per i-cell, candidates staged in
 //     shared memory, FP32 cut-off test with an FP64 re-test in a narrow band,
-//     hits compacted into 32-pair chunks of one i molecule;
+//     hits of consecutive i molecules packed into 32-pair chunks;
 //   * FP32 site-site math (rsqrt/rcp on the MUFU pipe);
-//   * i side: per-lane FP32 partials, one warp reduction per i, per-pass
-//     totals in shared memory;
-//   * Newton-3 side (half shell): the j's of a chunk are distinct, so the
-//     reactions go into per-warp shared accumulators with plain adds; each
-//     segment is flushed to global FP32 accumulators (one red per value per
-//     staged candidate) and a finalize kernel converts them to FP64;
+//   * i side: a segmented warp sum per chunk into per-pass totals in shared
+//     memory;
+//   * Newton-3 side (half shell): reactions into per-candidate shared
+//     accumulators, one i of a chunk at a time; each staged window is
+//     flushed with 16-byte vector reductions into FP32 accumulator records,
+//     read directly by the integrator and converted to FP64 only on demand;
 //   * full shell: each ordered pair from both sides, plain FP64 stores of
 //     the per-molecule totals, bitwise deterministic;
-//   * no FP64 arithmetic per pair: GB300's FP64 rate is ~1/70 of FP32.
+//   * no FP64 arithmetic per pair: GB300's FP64 rate is ~1/64 of FP32.
 #include "md_forceop.cuh"
 
 using namespace mdk;

@@ -4,16 +4,18 @@
 // Newton-3 half stencil) shared by the force, adjoint and batched kernels.
 //
 // Traversal (one warp per i-cell):
-//   * the stencil's candidate molecules are staged in shared memory with the
-//     periodic image offset already applied (FP32, i-cell frame);
-//   * for each i molecule all 32 lanes test 32 candidates at a time
+//   * the stencil cells' slots, counts and image offsets are loaded once
+//     (one lane per cell) and their candidate molecules staged in shared
+//     memory in windows of JCAP, image offset applied (FP32, i-cell frame);
+//   * for each i molecule the lanes test NTEST x 32 candidates per round
 //     (FP32 centre-of-mass distance; a test within a narrow band of r_c^2 is
 //     redone in FP64 from the FP64 state, so the pair set is the FP64
 //     definition's);
-//   * hits are ballot-compacted into a per-warp queue and handed to the
-//     pair operation 32 at a time, so the expensive site-site math runs on
-//     packed lanes (only ~16% of examined pairs interact, §3).
-//   * A chunk holds pairs of one i molecule, so its j's are distinct.
+//   * hits are ballot-compacted into a per-warp queue shared by the i
+//     molecules of a pass and handed to the pair operation 32 at a time, so
+//     the expensive site-site math runs on packed lanes (only ~16% of the
+//     examined pairs interact, §3); the lanes of one i in a chunk are
+//     contiguous and their j's distinct.
 #pragma once
 
 #include "md_internal.cuh"
