@@ -203,10 +203,12 @@ def main():
     ap.add_argument("--shell", default="half", choices=["half", "full"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="2cljq", choices=["2cljq", "batch", "adjoint", "lj", "slab", "lj200m"],
+    ap.add_argument("--workload", default="2cljq",
+                    choices=["2cljq", "batch", "adjoint", "lj", "slab", "lj200m", "sweep"],
                     help="2cljq: the headline step; batch: 512 uneven replicas; adjoint: parameter gradients; "
                          "lj: LJTS fluid N=4096; slab: vapour-liquid slab N=4,194,304; "
-                         "lj200m: homogeneous LJTS N=200M, one force evaluation")
+                         "lj200m: homogeneous LJTS N=200M, one force evaluation; "
+                         "sweep: LJTS fluid time per molecule-step for N = 4096 ... 16.8M")
     ap.add_argument("--replicas", type=int, default=512)
     ap.add_argument("--configs", type=int, default=4, help="adjoint workload: configurations per ensemble")
     args = ap.parse_args()
@@ -230,6 +232,8 @@ def main():
         return run_adjoint(args, md, torch, dev, rank)
     if args.workload in ("lj", "slab", "lj200m"):
         return run_single(args, md, torch, dev, rank)
+    if args.workload == "sweep":
+        return run_sweep(args, md, torch, dev, rank)
     cfg = mdgen.config_2cljq(seed_k=rank)
     half = args.shell == "half"
     sysm = md.System(cfg, deterministic=0 if half else 1, half_shell=1 if half else 0)
@@ -404,6 +408,41 @@ def run_single(args, md, torch, dev, rank):
                          "frac": achieved / peak, "traffic": None, "kernel": "k_force (LJ, half shell)",
                          "flops_per_pair": fpp},
             "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_sweep(args, md, torch, dev, rank):
+    """Cost of one md step against system size (the paper's O(N) linked-cell
+    scaling, §5): the LJTS fluid of config 1 (rho = 0.6, T = 0.95, r_c = 2.5,
+    dt = 0.002) for N = 4^6 ... 4^12, ms per step and ns per molecule-step."""
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for n in [4096 * 4 ** k for k in range(7)]:
+        cfg = mdgen.config_lj_fluid(n=n)
+        s = md.System(cfg, deterministic=0, half_shell=1)
+        s.set(cfg["r"], cfg["q"], cfg["v"], cfg["j"])
+        for _ in range(args.warmup):
+            s.step(1, cfg["dt"])
+        o = s.observables()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            s.step(1, cfg["dt"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / args.steps
+        s.close()
+        rows.append({"n": n, "ms_per_step": t, "ns_per_molecule_step": 1e6 * t / n,
+                     "mol_pairs_per_step": o["n_mol_pairs"]})
+    big = rows[-1]
+    line = {"metric": METRIC, "value": big["n"] / (big["ms_per_step"] / 1e3), "unit": "molecule updates/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": big["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 site math, f64 accumulation/state", "data": "synthetic (seeded)",
+            "config": {"workload": "LJTS fluid rho=0.6 T=0.95 rc=2.5 size sweep (one md step each)", "shell": "half"},
+            "sweep": rows}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
