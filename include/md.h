@@ -161,7 +161,11 @@ md_status md_compute_forces(md_system *sys, void *cuda_stream);
  * the half-step state (v, j at t + dt/2, q at t + dt; dof = 3N - 3 + N x
  * rotational dof); positions and orientations of the step are unchanged.
  * Computes forces first if they are stale.  Asynchronous (the factor is
- * computed and applied on the device). */
+ * computed and applied on the device).  For n_steps >= 2 (profiling off)
+ * pairs of steps are captured once as a CUDA graph per cell-buffer parity,
+ * dt and T_target and replayed; the result is that of n_steps single steps
+ * (bitwise with the deterministic full shell).  A graph is dropped when
+ * the molecules or parameters change. */
 md_status md_step(md_system *sys, int32_t n_steps, double dt, double T_target, void *cuda_stream);
 
 /* Synchronising read-back of the observables at the current time t:

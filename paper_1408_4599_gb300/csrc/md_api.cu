@@ -70,6 +70,11 @@ struct md_system {
     std::vector<PendingTiming> pending;
     std::vector<cudaEvent_t> pool;
     md_kernel_times times;
+    // md_step replays two captured steps per graph launch: one executable
+    // graph per buffer parity (the ping-pong state buffers swap every step)
+    cudaGraphExec_t gexec[2];
+    double gdt[2], gT[2];
+    int parity;
 };
 
 namespace {
@@ -479,8 +484,18 @@ md_status alloc_molecules(md_system *s, long long n)
     return MD_OK;
 }
 
+void drop_step_graphs(md_system *s)
+{
+    for (int p = 0; p < 2; p++)
+        if (s->gexec[p]) {
+            cudaGraphExecDestroy(s->gexec[p]);
+            s->gexec[p] = nullptr;
+        }
+}
+
 void free_all(md_system *s)
 {
+    drop_step_graphs(s);
     DevState &d = s->d;
     void *ptrs[] = {d.r, d.v, d.q, d.j, d.r2, d.v2, d.q2, d.j2, d.ids, d.ids2, d.F, d.tau, d.cell, d.cell_count,
                     d.cell_start, d.cell_fill, d.perm, d.perm2, d.com, d.geo, d.scan_tmp, d.partials,
@@ -532,6 +547,25 @@ md_status do_force(md_system *s, cudaStream_t st)
     s->forces_valid = true;
     s->f_in_acc = s->half_eff != 0;
     return MD_OK;
+}
+
+// One leapfrog step (§3) on stream st: integrate (+ NVT factor, §2) ->
+// rebuild (the factor applied in the reorder) -> forces.  The integrator
+// reads the forces where the force kernel leaves them: the FP32 records in
+// the half shell, the FP64 arrays in the full shell.
+md_status one_step(md_system *s, double dt, double T_target, cudaStream_t st)
+{
+    const bool nvt = T_target > 0.0;
+    const double dof = 3.0 * (double)s->d.n - 3.0 + (double)s->m.rot_dof * (double)s->d.n;
+    const bool thermo = nvt && dof > 0.0 && s->d.n > 0;
+    {
+        TimeScope ts(s, st, 0);
+        CK(launch_integrate(s->g, s->m, s->d, dt, s->half_eff, st), "integrate kernel");
+        if (thermo) CK(launch_thermostat(s->m, s->d, s->n_kin_blocks, T_target, dof, st), "thermostat kernels");
+    }
+    md_status ms = do_rebuild(s, st, false, thermo ? s->d.thermo : nullptr);
+    if (ms != MD_OK) return ms;
+    return do_force(s, st);
 }
 
 // FP64 F and tau for the callers that read them (observables, md_get_forces):
@@ -679,6 +713,8 @@ md_status md_set_molecules(md_system *s, int64_t n, const int32_t *comp_id, cons
     }
     // values are validated on the device by the preparation kernel (one
     // pass over the copied state instead of a host scan of the input)
+    drop_step_graphs(s);
+    s->parity = 0;
     md_status ms = alloc_molecules(s, n);
     if (ms != MD_OK) return ms;
     DevState &d = s->d;
@@ -757,20 +793,51 @@ md_status md_step(md_system *s, int32_t n_steps, double dt, double T_target, voi
         md_status ms = md_compute_forces(s, st);
         if (ms != MD_OK) return ms;
     }
-    // NVT (§2): velocity rescaling after every step, folded into the reorder
-    const bool nvt = T_target > 0.0;
-    const double dof = 3.0 * (double)s->d.n - 3.0 + (double)s->m.rot_dof * (double)s->d.n;
-    for (int k = 0; k < n_steps; k++) {
-        {
-            TimeScope ts(s, st, 0);
-            CK(launch_integrate(s->g, s->m, s->d, dt, s->f_in_acc ? 1 : 0, st), "integrate kernel");
-            if (nvt && dof > 0.0 && s->d.n > 0)
-                CK(launch_thermostat(s->m, s->d, s->n_kin_blocks, T_target, dof, st), "thermostat kernels");
+    int k = 0;
+    if (!s->profiling && n_steps >= 2 && s->d.n > 0) {
+        // pairs of steps as replays of a captured graph (the buffer assignment
+        // is back where it started after two steps)
+        for (; k + 2 <= n_steps; k += 2) {
+            const int p = s->parity;
+            if (!s->gexec[p] || s->gdt[p] != dt || s->gT[p] != T_target) {
+                if (s->gexec[p]) cudaGraphExecDestroy(s->gexec[p]);
+                s->gexec[p] = nullptr;
+                cudaStream_t cs;
+                CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+                cudaGraph_t graph;
+                cudaError_t eb = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+                if (eb != cudaSuccess) {
+                    cudaStreamDestroy(cs);
+                    CK(eb, "begin capture");
+                }
+                const DevState saved = s->d;
+                md_status ms = one_step(s, dt, T_target, cs);
+                if (ms == MD_OK) ms = one_step(s, dt, T_target, cs);
+                const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+                s->d = saved;  // captured, not run: the state has not moved
+                cudaStreamDestroy(cs);
+                if (ms != MD_OK) {
+                    if (ec == cudaSuccess) cudaGraphDestroy(graph);
+                    return ms;
+                }
+                CK(ec, "end capture");
+                const cudaError_t ei = cudaGraphInstantiate(&s->gexec[p], graph, 0);
+                cudaGraphDestroy(graph);
+                CK(ei, "graph instantiate");
+                s->gdt[p] = dt;
+                s->gT[p] = T_target;
+            }
+            CK(cudaGraphLaunch(s->gexec[p], st), "graph launch");
+            s->forces_valid = true;
+            s->f_in_acc = s->half_eff != 0;
+            s->step += 2;
+            s->time += 2.0 * dt;
         }
-        md_status ms = do_rebuild(s, st, false, nvt && dof > 0.0 && s->d.n > 0 ? s->d.thermo : nullptr);
+    }
+    for (; k < n_steps; k++) {
+        md_status ms = one_step(s, dt, T_target, st);
         if (ms != MD_OK) return ms;
-        ms = do_force(s, st);
-        if (ms != MD_OK) return ms;
+        s->parity ^= 1;
         s->step++;
         s->time += dt;
     }
@@ -916,6 +983,7 @@ md_status md_get_params(md_system *s, double *theta)
 md_status md_set_params(md_system *s, const double *theta, int32_t n_params)
 {
     if (!s || !theta) return MD_ERR_ARG;
+    drop_step_graphs(s);  // the model is a captured kernel argument
     if (n_params != md_n_params(s)) {
         set_err(s, "md_set_params: expected %d parameters, got %d", md_n_params(s), n_params);
         return MD_ERR_ARG;

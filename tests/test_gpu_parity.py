@@ -384,3 +384,31 @@ def test_runtime_signature_model_trajectory():
     cfg["v"] *= 0.3
     cfg["j"] *= 0.3
     _traj_compare(cfg, 10, 1e-5)
+
+
+@pytest.mark.parametrize("T_target", [0.0, 1.3])
+def test_step_graph_replay_equals_single_steps(T_target):
+    """md_step(n >= 2) replays captured pairs of steps (per buffer parity);
+    in the deterministic full shell the result is bitwise that of n calls of
+    md_step(1), across parities, a change of dt and the observables."""
+    cfg = mdgen.config_2cljq(n=6000)
+    res = []
+    for graphs in (False, True):
+        s = md.System(cfg, deterministic=1)
+        s.set(cfg["r"], cfg["q"], cfg["v"], cfg["j"])
+        plan = [(5, 0.001), (4, 0.001), (3, 0.0005)]
+        for n, dt in plan:
+            if graphs:
+                s.step(n, dt, T_target=T_target)
+            else:
+                for _ in range(n):
+                    s.step(1, dt, T_target=T_target)
+        o = s.observables()
+        res.append((s.molecules(), s.forces(), o))
+        s.close()
+    (m0, f0, o0), (m1, f1, o1) = res
+    for a, b in zip(m0 + f0, m1 + f1):
+        assert np.array_equal(a, b)
+    assert o0["step"] == o1["step"] == 12
+    for k in ("U_pot", "W", "K_trans", "K_rot", "n_mol_pairs", "time"):
+        assert o0[k] == o1[k], k
