@@ -24,8 +24,10 @@ struct ForceArgs {
 
 template <bool HALF>
 struct ForceExtra {
-    float jacc[HALF ? 6 : 1][JCAP];  // Newton-3 reactions: F (3), tau (3)
-    float ipart[32][6];              // i totals of the pass: F (3), tau (3)
+    float4 jf[HALF ? JCAP : 1];  // Newton-3 reactions: F, tau_x
+    float2 jt[HALF ? JCAP : 1];  // tau_y, tau_z
+    float4 if4[32];              // i totals of the pass: F, tau_x
+    float2 it2[32];              // tau_y, tau_z
 };
 
 template <class SIG, bool HALF>
@@ -52,15 +54,19 @@ struct ForceOp {
     __device__ void pass_begin(int ig_, int ni, int lane)
     {
         ig = ig_;
-        for (int t = lane; t < ni * 6; t += 32) (&T->x.ipart[0][0])[t] = 0.f;
+        for (int t = lane; t < ni; t += 32) {
+            T->x.if4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+            T->x.it2[t] = make_float2(0.f, 0.f);
+        }
         cU = cW = cX = cY = cZ = 0.f;
     }
     __device__ void seg_begin(Tile &TT, int nj, int lane)
     {
         if (HALF)
-            for (int t = lane; t < nj; t += 32)
-#pragma unroll
-                for (int q = 0; q < NQ; q++) TT.x.jacc[q][t] = 0.f;
+            for (int t = lane; t < nj; t += 32) {
+                TT.x.jf[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (NQ == 6) TT.x.jt[t] = make_float2(0.f, 0.f);
+            }
     }
     __device__ void count_examined(int n) { nexam += n; }
     __device__ void pair(Tile &, const IMol<SIG> &I, int, float X0, float X1, float X2, int js)
@@ -91,36 +97,40 @@ struct ForceOp {
     // sum over the lanes; the first lane of each i adds the i's total.
     __device__ void chunk_end(Tile &TT, int il, int k, bool valid, int lane)
     {
+        const int nvalid = __popc(__ballot_sync(FULLMASK, valid));  // valid lanes are a prefix
         const int prev = __shfl_up_sync(FULLMASK, il, 1);
         const bool head = valid && (lane == 0 || prev != il);
+        const unsigned hm0 = __ballot_sync(FULLMASK, head);
         if (HALF) {
-            float *J = &TT.x.jacc[0][0];
-            unsigned hm = __ballot_sync(FULLMASK, head);
-            while (hm) {  // warp-uniform
+            unsigned hm = hm0;
+            while (hm) {  // warp-uniform: one i of the chunk at a time
                 const int h = __ffs(hm) - 1;
                 hm &= hm - 1;
-                const int ilh = __shfl_sync(FULLMASK, il, h);  // every lane takes part in the shuffle
-                if (valid && il == ilh) {
-                    J[0 * JCAP + k] -= pF0;
-                    J[1 * JCAP + k] -= pF1;
-                    J[2 * JCAP + k] -= pF2;
+                const int e = hm ? __ffs(hm) - 1 : nvalid;
+                if (lane >= h && lane < e) {
+                    float4 a = TT.x.jf[k];
+                    a.x -= pF0;
+                    a.y -= pF1;
+                    a.z -= pF2;
                     if (NQ == 6) {
-                        J[3 * JCAP + k] += tq0;
-                        J[4 * JCAP + k] += tq1;
-                        J[5 * JCAP + k] += tq2;
+                        a.w += tq0;
+                        float2 b = TT.x.jt[k];
+                        b.x += tq1;
+                        b.y += tq2;
+                        TT.x.jt[k] = b;
                     }
+                    TT.x.jf[k] = a;
                 }
                 __syncwarp();
             }
         }
+        // lanes after this one in the same i segment
+        const unsigned later = hm0 & ~((2u << lane) - 1u);
+        const int rem = (later ? __ffs(later) - 1 : nvalid) - lane - 1;
         float v[6] = {pF0, pF1, pF2, pT0, pT1, pT2};
-        if (!valid)
-#pragma unroll
-            for (int q = 0; q < 6; q++) v[q] = 0.f;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const int ol = __shfl_down_sync(FULLMASK, il, off);
-            const bool take = lane + off < 32 && ol == il;
+            const bool take = off <= rem;
 #pragma unroll
             for (int q = 0; q < NQ; q++) {
                 const float o = __shfl_down_sync(FULLMASK, v[q], off);
@@ -128,9 +138,18 @@ struct ForceOp {
             }
         }
         if (head) {
-            float *ip = T->x.ipart[il];
-#pragma unroll
-            for (int q = 0; q < NQ; q++) ip[q] += v[q];
+            float4 a = T->x.if4[il];
+            a.x += v[0];
+            a.y += v[1];
+            a.z += v[2];
+            if (NQ == 6) {
+                a.w += v[3];
+                float2 b = T->x.it2[il];
+                b.x += v[4];
+                b.y += v[5];
+                T->x.it2[il] = b;
+            }
+            T->x.if4[il] = a;
         }
     }
     __device__ void seg_end(Tile &TT, int nj, int lane)
@@ -139,15 +158,21 @@ struct ForceOp {
             for (int t = lane; t < nj; t += 32) {
                 const int js = __float_as_int(TT.jc[t].w);
                 float *a = A.acc + (long long)FACC_STRIDE * js;
-                red_add_v4(a, TT.x.jacc[0][t], TT.x.jacc[1][t], TT.x.jacc[2][t], 0.f);
-                if (NQ == 6) red_add_v4(a + 4, TT.x.jacc[3][t], TT.x.jacc[4][t], TT.x.jacc[5][t], 0.f);
+                const float4 f = TT.x.jf[t];
+                red_add_v4(a, f.x, f.y, f.z, 0.f);
+                if (NQ == 6) {
+                    const float2 b = TT.x.jt[t];
+                    red_add_v4(a + 4, f.w, b.x, b.y, 0.f);
+                }
             }
     }
     __device__ void pass_end(int s0, int ig_, int ni, int lane)
     {
         for (int t = lane; t < ni; t += 32) {
             const int si = s0 + ig_ + t;
-            const float *ip = T->x.ipart[t];
+            const float4 i4 = T->x.if4[t];
+            const float2 i2 = T->x.it2[t];
+            const float ip[6] = {i4.x, i4.y, i4.z, i4.w, i2.x, i2.y};
             if (HALF || A.to_acc) {
                 float *a = A.acc + (long long)FACC_STRIDE * si;
                 red_add_v4(a, ip[0], ip[1], ip[2], 0.f);
