@@ -543,7 +543,8 @@ md_status do_rebuild(md_system *s, cudaStream_t st, bool need_cellid, const doub
 md_status do_force(md_system *s, cudaStream_t st)
 {
     TimeScope ts(s, st, 3);
-    CK(launch_force(s->g, s->m, s->d, s->half_eff, s->n_force_blocks, st), "force kernel");
+    // cells in counter order unless the energy sums must group identically on every launch
+    CK(launch_force(s->g, s->m, s->d, s->half_eff, !s->opt.deterministic, s->n_force_blocks, st), "force kernel");
     s->forces_valid = true;
     s->f_in_acc = s->half_eff != 0;
     return MD_OK;
@@ -665,7 +666,8 @@ md_status md_create(const double box[3], double cutoff, const md_site_types *typ
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.cell_start, sizeof(int) * (ncell + 1));
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.cell_fill, sizeof(int) * ncell);
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.scan_tmp, sizeof(int) * (scan_blocks(ncell) + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&d.partials, sizeof(double) * P_COUNT * s->n_force_blocks);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d.partials, sizeof(double) * (P_COUNT * (size_t)s->n_force_blocks + 1));
+    d.cell_ctr = e == cudaSuccess ? reinterpret_cast<unsigned *>(d.partials + P_COUNT * (size_t)s->n_force_blocks) : nullptr;
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.kin_partials, sizeof(double) * 4 * s->n_kin_blocks);
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.thermo, sizeof(double) * 2);
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.flags, sizeof(int) * 4);

@@ -178,7 +178,7 @@ __global__ void k_reorder_pack_b(const RepGrid *G, const int *rep, DevModel m, D
 }
 
 struct BatchArgs {
-    ForceArgs f;  // model, packed data, accumulators (grid fields unused)
+    ForceArgs f;  // model, packed data, accumulators (grid fields and cell_ctr unused)
     const RepGrid *grids;
     const int *rep_of_cell;
     const int *work;
@@ -408,6 +408,7 @@ BatchArgs batch_args(md_batch *b, bool half_list)
     B.f.partials = nullptr;
     B.f.flags = b->d.flags;
     B.f.to_acc = 1;
+    B.f.cell_ctr = nullptr;
     B.grids = b->dgrids;
     B.rep_of_cell = b->rep_of_cell;
     B.work = half_list ? b->work : b->work + b->n_work_half;

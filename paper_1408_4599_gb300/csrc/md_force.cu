@@ -50,8 +50,24 @@ __global__ void __launch_bounds__(MD_WARPS * 32, force_min_blocks<SIG>()) k_forc
     gv.bandf = A.g.bandf;
     gv.cell0 = 0;
     Op op(m, A, K, T);
-    for (long long c = (long long)blockIdx.x * MD_WARPS + warp; c < A.g.ncell; c += (long long)gridDim.x * MD_WARPS)
-        traverse_cell<SIG, HALF>(m, gv, A.cell_start, A.com, A.geo, A.r, K, c, *T, op, lane);
+    if (A.cell_ctr) {
+        // cells one at a time in counter order: a warp that finishes early
+        // takes the next cell (cell costs vary with the occupation).  The
+        // next index is claimed only once the current cell is done; claiming
+        // it ahead measured slower (the tail is balanced one cell later).
+        for (;;) {
+            unsigned c = 0;
+            if (lane == 0) c = atomicAdd(A.cell_ctr, 1u);
+            c = __shfl_sync(FULLMASK, c, 0);
+            if (c >= A.g.ncell) break;
+            traverse_cell<SIG, HALF>(m, gv, A.cell_start, A.com, A.geo, A.r, K, (long long)c, *T, op, lane);
+        }
+    } else {
+        // fixed grid stride: the same cells per warp on every launch, so the
+        // block partials of the energy and virial sum in a fixed grouping
+        for (long long c = (long long)blockIdx.x * MD_WARPS + warp; c < A.g.ncell; c += (long long)gridDim.x * MD_WARPS)
+            traverse_cell<SIG, HALF>(m, gv, A.cell_start, A.com, A.geo, A.r, K, c, *T, op, lane);
+    }
 
     // block partials: FP32 warp sums of the compensated lane sums; FP64 only
     // once per value per block
@@ -132,7 +148,8 @@ struct LaunchForce {
 
 int force_blocks_default() { return 152 * 16; }
 
-cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half_shell, int n_blocks, cudaStream_t s)
+cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half_shell, int dynamic_cells, int n_blocks,
+                         cudaStream_t s)
 {
     ForceArgs A;
     A.g = g;
@@ -148,8 +165,10 @@ cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half
     A.partials = d.partials;
     A.flags = d.flags;
     A.to_acc = 0;
-    // the grid may be smaller than the partials buffer: unused slots read as 0
-    cudaError_t e = cudaMemsetAsync(d.partials, 0, sizeof(double) * P_COUNT * n_blocks, s);
+    A.cell_ctr = dynamic_cells ? d.cell_ctr : nullptr;
+    // the grid may be smaller than the partials buffer: unused slots read as
+    // 0; the counter slot after the partials is cleared with them
+    cudaError_t e = cudaMemsetAsync(d.partials, 0, sizeof(double) * (P_COUNT * (size_t)n_blocks + 1), s);
     if (e != cudaSuccess) return e;
     if (half_shell) {
         e = cudaMemsetAsync(d.facc, 0, sizeof(float) * FACC_STRIDE * (d.n > 0 ? d.n : 1), s);

@@ -20,6 +20,7 @@ struct ForceArgs {
     double *partials;
     int *flags;
     int to_acc;       // full shell: also accumulate into acc (batched replicas of mixed shells)
+    unsigned *cell_ctr;  // non-null: cells are handed out one at a time from this counter
 };
 
 template <bool HALF>

@@ -72,7 +72,8 @@ struct DevState {
     float4 *com;                    // n: centre of mass relative to its cell centre
     float4 *geo;                    // n * K: site offsets then axes (space frame)
     int *scan_tmp;                  // block sums of the scan
-    double *partials;               // force-kernel block partials, 8 per block
+    double *partials;               // force-kernel block partials, 8 per block, then one counter slot
+    unsigned *cell_ctr;             // in that last slot: cells handed out by the force kernel
     double *kin_partials;           // kinetic partials, 4 per block ([2], [3]: half-step K for the thermostat)
     double *thermo;                 // [0] velocity-rescaling factor of the last step, [1] its T_half
     int *flags;                     // [0] non-finite, [1] overflow, [2] timeout
@@ -115,7 +116,7 @@ cudaError_t launch_sort(long long ncell, DevState &d, cudaStream_t s);
 void swap_state(DevState &d);
 // half shell: the results stay in the FP32 accumulators d.facc until
 // launch_force_finalize; full shell: FP64 d.F, d.tau directly.
-cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half_shell, int n_blocks,
+cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half_shell, int dynamic_cells, int n_blocks,
                          cudaStream_t s);
 // acc32: read the forces from d.facc instead of d.F, d.tau
 cudaError_t launch_integrate(const Grid &g, const DevModel &m, DevState &d, double dt, int acc32, cudaStream_t s);
