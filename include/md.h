@@ -98,7 +98,10 @@ typedef struct {
     double eps_rf;           /* reaction-field continuum permittivity; INFINITY allowed (§3) */
     int32_t lj_shift;        /* 1: truncated-shifted LJ (LJTS, §2) */
     int32_t lj_lrc;          /* 1: report the isotropic long-range correction (§3) */
-    int32_t deterministic;   /* 1: bitwise run-to-run reproducible (full-shell, no atomics) */
+    int32_t deterministic;   /* 1: bitwise run-to-run reproducible (full shell, no atomics, cells
+                              *    assigned to warps by a fixed stride).  0: cells are handed out
+                              *    from a counter, so the energy, virial and md_param_grad sums
+                              *    group differently per launch (last-bit differences) */
     int32_t half_shell;      /* 1: Newton-3 half-shell cell pairs (§3 figure on cell enumeration) */
 } md_options;
 

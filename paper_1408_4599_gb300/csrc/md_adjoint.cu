@@ -75,6 +75,7 @@ struct AdjArgs {
     const double *r;
     double *partials;  // [block][NACC]
     int nacc;
+    unsigned *cell_ctr;  // non-null: cells handed out from this counter
 };
 
 struct AdjExtra {
@@ -226,8 +227,9 @@ __global__ void __launch_bounds__(MD_WARPS * 32) k_adjoint(const __grid_constant
     gv.bandf = A.g.bandf;
     gv.cell0 = 0;
     Op op(m, A, K);
-    for (long long c = (long long)blockIdx.x * MD_WARPS + warp; c < A.g.ncell; c += (long long)gridDim.x * MD_WARPS)
+    for_each_cell(A.g.ncell, A.cell_ctr, warp, lane, [&](long long c) {
         traverse_cell<SIG, HALF>(m, gv, A.cell_start, A.com, A.geo, A.r, K, c, *T, op, lane);
+    });
     __shared__ float s_red[MD_WARPS][LY::NACC];
 #pragma unroll
     for (int q = 0; q < LY::NACC; q++) {
@@ -281,8 +283,8 @@ struct NaccOf {
 // Accumulator count of the adjoint kernel for this model (-1: not compiled).
 int adjoint_nacc(const DevModel &m) { return dispatch_sig(m, NaccOf{}); }
 
-cudaError_t launch_adjoint(const Grid &g, const DevModel &m, const DevState &d, int half_shell, int n_blocks,
-                           double *partials, int nacc, cudaStream_t s)
+cudaError_t launch_adjoint(const Grid &g, const DevModel &m, const DevState &d, int half_shell, int dynamic_cells,
+                           int n_blocks, double *partials, int nacc, cudaStream_t s)
 {
     AdjArgs A;
     A.g = g;
@@ -293,5 +295,10 @@ cudaError_t launch_adjoint(const Grid &g, const DevModel &m, const DevState &d, 
     A.r = d.r;
     A.partials = partials;
     A.nacc = nacc;
+    A.cell_ctr = dynamic_cells ? d.cell_ctr : nullptr;
+    if (A.cell_ctr) {
+        const cudaError_t e = cudaMemsetAsync(A.cell_ctr, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+    }
     return dispatch_sig(m, LaunchAdj{A, half_shell, n_blocks, s});
 }

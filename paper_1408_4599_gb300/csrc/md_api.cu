@@ -1037,7 +1037,9 @@ md_status md_param_grad(md_system *s, int32_t n_cfg, int64_t n, const double *r_
         if (ms != MD_OK) return ms;
         {
             TimeScope ts(s, st, 6);
-            CK(launch_adjoint(s->g, s->m, s->d, half, s->n_force_blocks, s->adj_partials, nacc, st), "adjoint kernel");
+            CK(launch_adjoint(s->g, s->m, s->d, half, !s->opt.deterministic, s->n_force_blocks, s->adj_partials,
+                              nacc, st),
+               "adjoint kernel");
         }
         CK(cudaMemcpyAsync(part.data(), s->adj_partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
            "copy adjoint partials");

@@ -50,24 +50,9 @@ __global__ void __launch_bounds__(MD_WARPS * 32, force_min_blocks<SIG>()) k_forc
     gv.bandf = A.g.bandf;
     gv.cell0 = 0;
     Op op(m, A, K, T);
-    if (A.cell_ctr) {
-        // cells one at a time in counter order: a warp that finishes early
-        // takes the next cell (cell costs vary with the occupation).  The
-        // next index is claimed only once the current cell is done; claiming
-        // it ahead measured slower (the tail is balanced one cell later).
-        for (;;) {
-            unsigned c = 0;
-            if (lane == 0) c = atomicAdd(A.cell_ctr, 1u);
-            c = __shfl_sync(FULLMASK, c, 0);
-            if (c >= A.g.ncell) break;
-            traverse_cell<SIG, HALF>(m, gv, A.cell_start, A.com, A.geo, A.r, K, (long long)c, *T, op, lane);
-        }
-    } else {
-        // fixed grid stride: the same cells per warp on every launch, so the
-        // block partials of the energy and virial sum in a fixed grouping
-        for (long long c = (long long)blockIdx.x * MD_WARPS + warp; c < A.g.ncell; c += (long long)gridDim.x * MD_WARPS)
-            traverse_cell<SIG, HALF>(m, gv, A.cell_start, A.com, A.geo, A.r, K, c, *T, op, lane);
-    }
+    for_each_cell(A.g.ncell, A.cell_ctr, warp, lane, [&](long long c) {
+        traverse_cell<SIG, HALF>(m, gv, A.cell_start, A.com, A.geo, A.r, K, c, *T, op, lane);
+    });
 
     // block partials: FP32 warp sums of the compensated lane sums; FP64 only
     // once per value per block

@@ -131,6 +131,6 @@ cudaError_t launch_prepare_input(const Grid &g, DevState &d, cudaStream_t s);
 int force_blocks_default();
 cudaError_t launch_force_finalize(DevState &d, cudaStream_t s);
 int adjoint_nacc(const DevModel &m);
-cudaError_t launch_adjoint(const Grid &g, const DevModel &m, const DevState &d, int half_shell, int n_blocks,
-                           double *partials, int nacc, cudaStream_t s);
+cudaError_t launch_adjoint(const Grid &g, const DevModel &m, const DevState &d, int half_shell, int dynamic_cells,
+                           int n_blocks, double *partials, int nacc, cudaStream_t s);
 int scan_blocks(long long ncell);

@@ -499,6 +499,30 @@ struct GridView {
     long long cell0;          // first global cell index of this grid
 };
 
+// Calls visit(c) once for every cell c < ncell, each cell by one warp of
+// the grid (warp = the warp's index in its block).  ctr non-null: cells
+// one at a time in counter order, the next claimed when the warp has
+// finished its cell (cell costs vary with the occupation, so warps that
+// finish early take more; claiming ahead balances the tail one cell later
+// and measured slower).  ctr null: a fixed grid stride, the same cells per
+// warp on every launch (fixed summation grouping of the block partials).
+template <class Visit>
+__device__ __forceinline__ void for_each_cell(long long ncell, unsigned *ctr, int warp, int lane, Visit &&visit)
+{
+    if (ctr) {
+        for (;;) {
+            unsigned c = 0;
+            if (lane == 0) c = atomicAdd(ctr, 1u);
+            c = __shfl_sync(FULLMASK, c, 0);
+            if (c >= ncell) break;
+            visit((long long)c);
+        }
+    } else {
+        for (long long c = (long long)blockIdx.x * MD_WARPS + warp; c < ncell; c += (long long)gridDim.x * MD_WARPS)
+            visit(c);
+    }
+}
+
 // Visits every interacting pair (i in cell c, j in the stencil) in chunks
 // of <= 32 pairs.  The hits of consecutive i molecules of a pass share a
 // queue, so a chunk may hold pairs of several i's (contiguous lanes per i,
