@@ -375,20 +375,29 @@ def run_single(args, md, torch, dev, rank):
     s.observables()
     md.md_profile(s.h, True)
     md.md_kernel_times_get(s.h)
+    # L2 flushed before every timed step unless the state alone exceeds the
+    # 129 MB L2 (the 200M point: ~70 GB on the device, no room for a buffer)
+    flush = None if evals_only else torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     clocks = ClockSampler(dev.index or 0)
     clocks.start()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        s.compute_forces() if evals_only else s.step(1, cfg["dt"])
-    e1.record(stream)
-    torch.cuda.synchronize()
+    t = timed_calls(lambda: s.compute_forces() if evals_only else s.step(1, cfg["dt"]), steps, stream, torch, flush)
     clk = clocks.stop()
-    t = e0.elapsed_time(e1) / 1e3
     kt = md.md_kernel_times_get(s.h)
     md.md_profile(s.h, False)
     o = s.observables()
+    graph = None
+    if not evals_only:
+        # the same steps as one md_step(steps) call (pairs of steps replayed as
+        # CUDA graphs), back to back: no flush between the steps of one call
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        s.step(steps, cfg["dt"])
+        g1.record(stream)
+        torch.cuda.synchronize()
+        graph = {"ms_per_step": g0.elapsed_time(g1) / steps,
+                 "note": f"one md_step({steps}) call (CUDA-graph replay), L2 not flushed between its steps"}
     s.close()
     fk = kt["force"]
     f_ms = fk["ms"] / max(fk["launches"], 1)
@@ -400,7 +409,8 @@ def run_single(args, md, torch, dev, rank):
     line = {"metric": METRIC, "value": o["n_site_pairs"] * steps / t, "unit": UNIT, "n_gpus": 1, "steps": steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 site math, f64 accumulation/state", "data": "synthetic (seeded)",
-            "config": {"workload": what, "shell": "half", "l2": "not flushed" if n < 1_000_000 else "working set > L2"},
+            "config": {"workload": what, "shell": "half",
+                       "l2": "working set > L2" if flush is None else "flushed (512 MB write) before every timed step"},
             "molecule_updates_per_s": None if evals_only else n * steps / t,
             "mol_pairs_per_eval": o["n_mol_pairs"], "force_ms_per_launch": f_ms,
             "kernel_ms_per_step": {k: v["ms"] / steps for k, v in kt.items() if v["launches"]},
@@ -408,15 +418,36 @@ def run_single(args, md, torch, dev, rank):
                          "frac": achieved / peak, "traffic": None, "kernel": "k_force (LJ, half shell)",
                          "flops_per_pair": fpp},
             "clocks": clk}
+    if graph is not None:
+        line["graph_replay"] = graph
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
+def timed_calls(fn, steps, stream, torch, flush=None):
+    """Device seconds of `steps` calls of fn, each bracketed by CUDA events
+    on the launch stream; with a flush buffer, it is overwritten (evicting L2)
+    before every call, outside the events."""
+    total_ms = 0.0
+    for _ in range(steps):
+        if flush is not None:
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    return total_ms / 1e3
+
+
 def run_sweep(args, md, torch, dev, rank):
     """Cost of one md step against system size (the paper's O(N) linked-cell
-    scaling, §5): the LJTS fluid of config 1 (rho = 0.6, T = 0.95, r_c = 2.5,
-    dt = 0.002) for N = 4^6 ... 4^12, ms per step and ns per molecule-step."""
+    scaling, §5): the LJTS fluid state point of the N = 4096 workload (rho =
+    0.6, T = 0.95, r_c = 2.5, dt = 0.002) for N = 4^6 ... 4^12, ms per step
+    and ns per molecule-step."""
     stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     rows = []
     for n in [4096 * 4 ** k for k in range(7)]:
         cfg = mdgen.config_lj_fluid(n=n)
@@ -426,22 +457,24 @@ def run_sweep(args, md, torch, dev, rank):
             s.step(1, cfg["dt"])
         o = s.observables()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            s.step(1, cfg["dt"])
-        e1.record(stream)
+        t = 1e3 * timed_calls(lambda: s.step(1, cfg["dt"]), args.steps, stream, torch, flush) / args.steps
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        s.step(args.steps, cfg["dt"])
+        g1.record(stream)
         torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / args.steps
+        tg = g0.elapsed_time(g1) / args.steps
         s.close()
         rows.append({"n": n, "ms_per_step": t, "ns_per_molecule_step": 1e6 * t / n,
-                     "mol_pairs_per_step": o["n_mol_pairs"]})
+                     "graph_replay_ms_per_step": tg, "mol_pairs_per_step": o["n_mol_pairs"]})
     big = rows[-1]
     line = {"metric": METRIC, "value": big["n"] / (big["ms_per_step"] / 1e3), "unit": "molecule updates/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": big["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 site math, f64 accumulation/state", "data": "synthetic (seeded)",
-            "config": {"workload": "LJTS fluid rho=0.6 T=0.95 rc=2.5 size sweep (one md step each)", "shell": "half"},
+            "config": {"workload": "LJTS fluid rho=0.6 T=0.95 rc=2.5 size sweep (one md step each)", "shell": "half",
+                       "l2": "flushed (512 MB write) before every timed md_step(1); graph_replay_ms_per_step: one "
+                             "md_step(steps) call, not flushed between its steps"},
             "sweep": rows}
     if rank == 0:
         print(json.dumps(line), flush=True)
