@@ -389,7 +389,9 @@ def run_single(args, md, torch, dev, rank):
     graph = None
     if not evals_only:
         # the same steps as one md_step(steps) call (pairs of steps replayed as
-        # CUDA graphs), back to back: no flush between the steps of one call
+        # CUDA graphs), back to back: no flush between the steps of one call;
+        # an untimed md_step(2) first captures the graph of this buffer parity
+        s.step(2, cfg["dt"])
         torch.cuda.synchronize()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record(stream)
@@ -458,6 +460,8 @@ def run_sweep(args, md, torch, dev, rank):
         o = s.observables()
         torch.cuda.synchronize()
         t = 1e3 * timed_calls(lambda: s.step(1, cfg["dt"]), args.steps, stream, torch, flush) / args.steps
+        s.step(2, cfg["dt"])  # untimed: captures the graph of this buffer parity
+        torch.cuda.synchronize()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record(stream)
         s.step(args.steps, cfg["dt"])
