@@ -44,7 +44,7 @@ def flops_per_pair():
     return int(re.search(r"#define MD_FLOPS_PAIR_2CLJQ (\d+)", txt).group(1))
 
 
-FORCE_SOURCES = ("md_force.cu", "md_forceop.cuh", "md_internal.cuh", "md_pair.cuh")
+FORCE_SOURCES = ("md_force.cu", "md_force.cuh", "md_forceop.cuh", "md_internal.cuh", "md_pair.cuh")
 
 
 def force_traffic():
@@ -201,6 +201,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--shell", default="half", choices=["half", "full"])
+    ap.add_argument("--cell-div", type=int, default=1, choices=[1, 2],
+                    help="cells per cut-off length: 1 (27-cell stencil) or 2 (125-cell stencil, §3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="2cljq",
@@ -236,7 +238,7 @@ def main():
         return run_sweep(args, md, torch, dev, rank)
     cfg = mdgen.config_2cljq(seed_k=rank)
     half = args.shell == "half"
-    sysm = md.System(cfg, deterministic=0 if half else 1, half_shell=1 if half else 0)
+    sysm = md.System(cfg, deterministic=0 if half else 1, half_shell=1 if half else 0, cell_div=args.cell_div)
     stream = torch.cuda.current_stream(dev)
     t = {k: torch.from_numpy(cfg[k]).to(dev) for k in ("r", "v", "q", "j")}
     sysm.set(t["r"], t["q"], t["v"], t["j"])
@@ -301,7 +303,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 site math, f64 accumulation/state",
             "data": "synthetic (seeded 2CLJQ fluid, random orientations)",
             "config": {"workload": "2CLJQ rigid-molecule fluid N=262144 rho=0.55 T=1 rc=3 dt=0.001 (one md step)",
-                       "shell": args.shell, "l2": "flushed (512 MB write) before every timed step",
+                       "shell": args.shell, "cells_per_cutoff": args.cell_div,
+                       "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "molecule_updates_per_s": mol_updates,
             "mol_pairs_per_step": mol_pairs / args.steps, "site_pairs_per_step": site_pairs / args.steps,
@@ -364,7 +367,7 @@ def run_single(args, md, torch, dev, rank):
         cfg, what = mdgen.config_lj_homogeneous(200_000_000), "homogeneous LJTS N=200M rho=0.73 rc=2.5 " \
                                                               "(one force evaluation)"
     stream = torch.cuda.current_stream(dev)
-    s = md.System(cfg, deterministic=0, half_shell=1)
+    s = md.System(cfg, deterministic=0, half_shell=1, cell_div=args.cell_div)
     s.set(cfg["r"], cfg["q"], cfg["v"], cfg["j"])
     n = cfg["r"].shape[0]
     del cfg["r"], cfg["v"], cfg["q"], cfg["j"]
@@ -411,7 +414,7 @@ def run_single(args, md, torch, dev, rank):
     line = {"metric": METRIC, "value": o["n_site_pairs"] * steps / t, "unit": UNIT, "n_gpus": 1, "steps": steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 site math, f64 accumulation/state", "data": "synthetic (seeded)",
-            "config": {"workload": what, "shell": "half",
+            "config": {"workload": what, "shell": "half", "cells_per_cutoff": args.cell_div,
                        "l2": "working set > L2" if flush is None else "flushed (512 MB write) before every timed step"},
             "molecule_updates_per_s": None if evals_only else n * steps / t,
             "mol_pairs_per_eval": o["n_mol_pairs"], "force_ms_per_launch": f_ms,
@@ -453,7 +456,7 @@ def run_sweep(args, md, torch, dev, rank):
     rows = []
     for n in [4096 * 4 ** k for k in range(7)]:
         cfg = mdgen.config_lj_fluid(n=n)
-        s = md.System(cfg, deterministic=0, half_shell=1)
+        s = md.System(cfg, deterministic=0, half_shell=1, cell_div=args.cell_div)
         s.set(cfg["r"], cfg["q"], cfg["v"], cfg["j"])
         for _ in range(args.warmup):
             s.step(1, cfg["dt"])
@@ -477,6 +480,7 @@ def run_sweep(args, md, torch, dev, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 site math, f64 accumulation/state", "data": "synthetic (seeded)",
             "config": {"workload": "LJTS fluid rho=0.6 T=0.95 rc=2.5 size sweep (one md step each)", "shell": "half",
+                       "cells_per_cutoff": args.cell_div,
                        "l2": "flushed (512 MB write) before every timed md_step(1); graph_replay_ms_per_step: one "
                              "md_step(steps) call, not flushed between its steps"},
             "sweep": rows}

@@ -103,6 +103,10 @@ typedef struct {
                               *    from a counter, so the energy, virial and md_param_grad sums
                               *    group differently per launch (last-bit differences) */
     int32_t half_shell;      /* 1: Newton-3 half-shell cell pairs (§3 figure on cell enumeration) */
+    int32_t cell_div;        /* cells per cut-off length (§3): 1 (or 0): edge >= cutoff, 27-cell
+                              *    stencil; 2: edge >= cutoff / 2, 125-cell stencil (15.6 instead
+                              *    of 27 cutoff^3 examined around each molecule).  Same pairs and
+                              *    results; the half shell needs >= 2 cell_div + 1 cells per axis */
 } md_options;
 
 typedef struct {
@@ -132,10 +136,10 @@ typedef struct {
 
 /* Creates a system: periodic box (edge lengths, each >= 2 cutoff), centre-
  * of-mass cut-off radius (§3), site types (§2) and options.  Cells of edge
- * >= cutoff, floor(L / cutoff) per axis (§3 linked cells).  Allocates no
- * per-molecule memory yet.  Errors: MD_ERR_ARG, MD_ERR_BOX,
- * MD_ERR_UNSUPPORTED (more than one component, > 8 merged sites or LJ
- * types).  *out is set only on MD_OK. */
+ * >= cutoff / cell_div, floor(cell_div L / cutoff) per axis (§3 linked
+ * cells).  Allocates no per-molecule memory yet.  Errors: MD_ERR_ARG (also
+ * cell_div not 0, 1 or 2), MD_ERR_BOX, MD_ERR_UNSUPPORTED (more than one
+ * component, > 8 merged sites or LJ types).  *out is set only on MD_OK. */
 md_status md_create(const double box[3], double cutoff, const md_site_types *types, const md_options *options,
                     md_system **out);
 
@@ -205,7 +209,8 @@ md_status md_set_params(md_system *sys, const double *theta, int32_t n_params);
  * n_cfg x n x 4 (host or device per on_device).  dU, dW: P doubles (host);
  * means[2] = <U>, <W> (host).  Synchronising.  The system is left holding
  * the last configuration with stale forces.  Errors: MD_ERR_ARG,
- * MD_ERR_UNSUPPORTED (site signature without a compiled adjoint). */
+ * MD_ERR_UNSUPPORTED (site signature without a compiled adjoint, or a
+ * system created with cell_div = 2). */
 md_status md_param_grad(md_system *sys, int32_t n_cfg, int64_t n, const double *r_all, const double *q_all,
                         int32_t on_device, double *dU, double *dW, double *means, void *cuda_stream);
 
@@ -230,7 +235,8 @@ md_status md_kernel_times_get(md_system *sys, md_kernel_times *out);
  * options->half_shell is set, smaller boxes the full stencil.
  *
  * md_batch_create: boxes n_sys x 3 (host), each edge >= 2 cutoff.
- * Errors as md_create. */
+ * Errors as md_create; MD_ERR_UNSUPPORTED for options->cell_div = 2 (the
+ * replicas use cells of edge >= cutoff). */
 md_status md_batch_create(int32_t n_sys, const double *boxes, double cutoff, const md_site_types *types,
                           const md_options *options, md_batch **out);
 

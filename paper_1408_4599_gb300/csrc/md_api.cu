@@ -622,10 +622,12 @@ md_status md_create(const double box[3], double cutoff, const md_site_types *typ
         return MD_ERR_ARG;
     for (int k = 0; k < 3; k++)
         if (box[k] < 2.0 * cutoff) return MD_ERR_BOX;
-    md_options opt = {INFINITY, 0, 0, 1, 0};
+    md_options opt = {INFINITY, 0, 0, 1, 0, 1};
     if (options) opt = *options;
     if (std::isnan(opt.eps_rf) || (!std::isinf(opt.eps_rf) && opt.eps_rf < 1.0) || (std::isinf(opt.eps_rf) && opt.eps_rf < 0))
         return MD_ERR_ARG;
+    if (opt.cell_div == 0) opt.cell_div = 1;
+    if (opt.cell_div != 1 && opt.cell_div != 2) return MD_ERR_ARG;
     md_system *s = new (std::nothrow) md_system();
     if (!s) return MD_ERR_OOM;
     s->opt = opt;
@@ -637,9 +639,16 @@ md_status md_create(const double box[3], double cutoff, const md_site_types *typ
         return st;
     }
     Grid &g = s->g;
+    g.m = opt.cell_div;  // stencil radius in cells
     long long ncell = 1;
     for (int k = 0; k < 3; k++) {
-        int nc = (int)std::floor(box[k] / (cutoff * (1.0 + 1e-9)));
+        // edge >= cutoff / m: the stencil's m cells per side cover the cut-off
+        const double nd = std::floor(box[k] * g.m / (cutoff * (1.0 + 1e-9)));
+        if (nd > 2e9) {
+            delete s;
+            return MD_ERR_UNSUPPORTED;
+        }
+        int nc = (int)nd;
         g.nc[k] = nc < 1 ? 1 : nc;
         g.L[k] = box[k];
         g.ell[k] = box[k] / g.nc[k];
@@ -655,7 +664,9 @@ md_status md_create(const double box[3], double cutoff, const md_site_types *typ
     g.rc2 = cutoff * cutoff;
     g.rc2f = (float)g.rc2;
     g.bandf = (float)(2e-5 * g.rc2);
-    s->half_eff = (opt.half_shell && !opt.deterministic && g.nc[0] >= 3 && g.nc[1] >= 3 && g.nc[2] >= 3) ? 1 : 0;
+    // the half stencil counts each pair once only if its cells are distinct
+    const int nmin = 2 * g.m + 1;
+    s->half_eff = (opt.half_shell && !opt.deterministic && g.nc[0] >= nmin && g.nc[1] >= nmin && g.nc[2] >= nmin) ? 1 : 0;
     s->d.K = s->m.single_lj_at_com ? 0 : (s->m.linear ? 1 : s->m.S + s->m.NA);
 
     long long fb = (ncell + MD_WARPS - 1) / MD_WARPS;
@@ -1018,6 +1029,10 @@ md_status md_param_grad(md_system *s, int32_t n_cfg, int64_t n, const double *r_
     const int nacc = adjoint_nacc(s->m);
     if (nacc < 0) {
         set_err(s, "md_param_grad: the adjoint kernel is compiled for the built-in site signatures only");
+        return MD_ERR_UNSUPPORTED;
+    }
+    if (s->g.m != 1) {
+        set_err(s, "md_param_grad: the adjoint kernel traverses cells of edge >= cutoff (cell_div 1) only");
         return MD_ERR_UNSUPPORTED;
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;

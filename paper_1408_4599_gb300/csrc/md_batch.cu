@@ -520,8 +520,12 @@ md_status md_batch_create(int32_t n_sys, const double *boxes, double cutoff, con
                 delete b;
                 return MD_ERR_BOX;
             }
-    md_options opt = {INFINITY, 0, 0, 1, 1};
+    md_options opt = {INFINITY, 0, 0, 1, 1, 1};
     if (options) opt = *options;
+    if (opt.cell_div != 0 && opt.cell_div != 1) {  // replicas use cells of edge >= cutoff
+        delete b;
+        return opt.cell_div == 2 ? MD_ERR_UNSUPPORTED : MD_ERR_ARG;
+    }
     md_status st = md_create(boxes, cutoff, types, &opt, &b->tmpl);
     if (st != MD_OK) {
         delete b;

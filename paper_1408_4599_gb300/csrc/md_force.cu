@@ -1,86 +1,11 @@
-// md_force.cu -- linked-cell force / torque / energy / virial kernel (§3:
-// force and torque calculation over the 27-cell stencil or the 14-cell
-// Newton-3 stencil, then summation per molecule) for rigid molecules of LJ
-// centres and point charges, dipoles and linear quadrupoles (§2).
-//
-// GB300 design (CUDA cores -- this is not a dense contraction):
-//   * traversal of md_pair.cuh: one warp per i-cell, candidates staged in
-//     shared memory, FP32 cut-off test with an FP64 re-test in a narrow band,
-//     hits of consecutive i molecules packed into 32-pair chunks;
-//   * FP32 site-site math (rsqrt/rcp on the MUFU pipe);
-//   * i side: a segmented warp sum per chunk into per-pass totals in shared
-//     memory;
-//   * Newton-3 side (half shell): reactions into per-candidate shared
-//     accumulators, one i of a chunk at a time; each staged window is
-//     flushed with 16-byte vector reductions into FP32 accumulator records,
-//     read directly by the integrator and converted to FP64 only on demand;
-//   * full shell: each ordered pair from both sides, plain FP64 stores of
-//     the per-molecule totals, bitwise deterministic;
-//   * no FP64 arithmetic per pair: GB300's FP64 rate is ~1/64 of FP32.
-#include "md_forceop.cuh"
+// md_force.cu -- launches of the linked-cell force kernel (md_force.cuh)
+// for cells of edge >= r_c (27- / 14-cell stencils) and the FP32 -> FP64
+// finalize of the half-shell accumulators.
+#include "md_force.cuh"
 
 using namespace mdk;
 
 namespace {
-
-// Resident blocks the register budget is sized for: 4 blocks of 4 warps (at
-// most 128 registers) for models of up to 3 merged sites, 3 blocks (168) for
-// the larger compiled signatures, whose site loops spill at 128 registers,
-// and 2 for the run-time signature.
-template <class SIG>
-constexpr int force_min_blocks() { return SIG::DYN ? 2 : (SIG::S <= 3 ? 4 : 3); }
-
-template <class SIG, bool HALF>
-__global__ void __launch_bounds__(MD_WARPS * 32, force_min_blocks<SIG>()) k_force(const __grid_constant__ ForceArgs A)
-{
-    using Op = ForceOp<SIG, HALF>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    typename Op::Tile *T = reinterpret_cast<typename Op::Tile *>(smem_raw) + warp;
-    const DevModel &m = A.m;
-    const int K = SIG::kk(m);
-    GridView gv;
-    for (int k = 0; k < 3; k++) {
-        gv.nc[k] = A.g.nc[k];
-        gv.ellf[k] = A.g.ellf[k];
-        gv.L[k] = A.g.L[k];
-    }
-    gv.rc2 = A.g.rc2;
-    gv.rc2f = A.g.rc2f;
-    gv.bandf = A.g.bandf;
-    gv.cell0 = 0;
-    Op op(m, A, K, T);
-    for_each_cell(A.g.ncell, A.cell_ctr, warp, lane, [&](long long c) {
-        traverse_cell<SIG, HALF>(m, gv, A.cell_start, A.com, A.geo, A.r, K, c, *T, op, lane);
-    });
-
-    // block partials: FP32 warp sums of the compensated lane sums; FP64 only
-    // once per value per block
-    float v[5] = {op.sU - op.kU, op.sW - op.kW, op.sX - op.kX, op.sY - op.kY, op.sZ - op.kZ};
-    for (int q = 0; q < 5; q++)
-        for (int msk = 16; msk > 0; msk >>= 1) v[q] += __shfl_xor_sync(FULLMASK, v[q], msk);
-    const int wm = __reduce_add_sync(FULLMASK, op.nmol), we = __reduce_add_sync(FULLMASK, op.nexam);
-    __shared__ float s_red[MD_WARPS][5];
-    __shared__ long long s_cnt[MD_WARPS][2];
-    if (lane == 0) {
-        for (int q = 0; q < 5; q++) s_red[warp][q] = v[q];
-        s_cnt[warp][0] = wm;
-        s_cnt[warp][1] = we;
-    }
-    __syncthreads();
-    if (threadIdx.x < P_COUNT) {
-        const double esc = HALF ? 1.0 : 0.5;  // the full shell visits every pair twice
-        const int q = threadIdx.x;
-        double t = 0.0;
-        for (int w = 0; w < MD_WARPS; w++) {
-            if (q == P_NMOL || q == P_NSITE) t += (double)s_cnt[w][0];
-            else if (q == P_NEXAM) t += (double)s_cnt[w][1];
-            else t += (double)s_red[w][q];
-        }
-        if (q == P_NSITE) t *= (double)m.site_pairs_per_mol_pair;
-        A.partials[(long long)blockIdx.x * P_COUNT + q] = esc * t;
-    }
-}
 
 // Half shell: FP32 accumulator records -> FP64 F, tau; non-finite check.
 __global__ void k_force_finalize(const float *acc, long long n, double *F, double *tau, int *flags)
@@ -97,37 +22,6 @@ __global__ void k_force_finalize(const float *acc, long long n, double *F, doubl
     }
     if (bad) atomicExch(&flags[FLAG_NONFINITE], 1);
 }
-
-struct LaunchForce {
-    const ForceArgs &A;
-    int half, n_blocks;
-    cudaStream_t s;
-    template <class SIG>
-    cudaError_t operator()() const
-    {
-        if (half) return run<SIG, true>();
-        return run<SIG, false>();
-    }
-    // persistent grid: as many blocks as can be resident (grid-stride over
-    // cells), never more than the cells need nor than the partials hold
-    template <class SIG, bool HALF>
-    cudaError_t run() const
-    {
-        const size_t sm = sizeof(typename ForceOp<SIG, HALF>::Tile) * MD_WARPS;
-        cudaFuncSetAttribute(k_force<SIG, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        int per_sm = 0, dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<SIG, HALF>, MD_WARPS * 32, sm);
-        long long want = (long long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-        const long long need = (A.g.ncell + MD_WARPS - 1) / MD_WARPS;
-        if (want > need) want = need;
-        if (want > n_blocks) want = n_blocks;
-        if (want < 1) want = 1;
-        k_force<SIG, HALF><<<(unsigned)want, MD_WARPS * 32, sm, s>>>(A);
-        return cudaGetLastError();
-    }
-};
 
 }  // namespace
 
@@ -159,7 +53,8 @@ cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half
         e = cudaMemsetAsync(d.facc, 0, sizeof(float) * FACC_STRIDE * (d.n > 0 ? d.n : 1), s);
         if (e != cudaSuccess) return e;
     }
-    return dispatch_sig(m, LaunchForce{A, half_shell, n_blocks, s});
+    if (g.m == 2) return launch_force_radius2(A, half_shell, n_blocks, s);
+    return dispatch_sig(m, LaunchForce<1>{A, half_shell, n_blocks, s});
 }
 
 cudaError_t launch_force_finalize(DevState &d, cudaStream_t s)

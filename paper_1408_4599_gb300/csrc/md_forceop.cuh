@@ -1,6 +1,6 @@
 // md_forceop.cuh -- the force / torque / energy / virial pair operation of
 // the linked-cell traversal (md_pair.cuh), shared by the single-system and
-// the batched-replica force kernels.  See md_force.cu for the design.
+// the batched-replica force kernels.  See md_force.cuh for the design.
 #pragma once
 
 #include "md_pair.cuh"

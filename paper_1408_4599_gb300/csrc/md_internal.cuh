@@ -47,7 +47,8 @@ struct Grid {
     int nc[3];
     long long ncell;
     double L[3];
-    double ell[3];                  // cell edge (>= rc)
+    int m;                          // stencil radius in cells: 1 (edge >= rc) or 2 (edge >= rc / 2)
+    double ell[3];                  // cell edge (>= rc / m)
     double iell[3];                 // 1 / ell
     float ellf[3];
     double rc2;

@@ -112,20 +112,27 @@ __host__ auto dispatch_sig(const DevModel &m, F &&f)
     return f.template operator()<SigDyn>();
 }
 
-// Half-shell stencil: the cell itself and the 13 neighbours that follow it
-// in (z, y, x) lexicographic order.
+// Stencil of M cells per axis around a cell (§3: M = 1 for cells of edge
+// >= r_c, the 27-cell stencil; M = 2 for cells of edge >= r_c / 2, the
+// 125-cell stencil).  Full stencil index f = (dz+M) W^2 + (dy+M) W + dx+M,
+// W = 2M+1.  The half (Newton-3) stencil is the cell itself (index 0) and
+// the (W^3 - 1)/2 cells that follow it in (z, y, x) lexicographic order.
+template <int M>
+struct Stencil {
+    static constexpr int W = 2 * M + 1;
+    static constexpr int FULL = W * W * W;
+    static constexpr int CENTRE = (FULL - 1) / 2;  // full index of the cell itself
+    static constexpr int HALFN = CENTRE + 1;       // half stencil size
+};
+
+template <int M>
 __device__ __forceinline__ void stencil_offset(bool half, int o, int &dx, int &dy, int &dz)
 {
-    if (half) {
-        const int h = o == 0 ? 13 : o + 13;  // the 13 forward offsets are full-stencil indices 14..26
-        dx = h % 3 - 1;
-        dy = (h / 3) % 3 - 1;
-        dz = h / 9 - 1;
-    } else {
-        dx = o % 3 - 1;
-        dy = (o / 3) % 3 - 1;
-        dz = o / 9 - 1;
-    }
+    using St = Stencil<M>;
+    const int f = half ? St::CENTRE + o : o;  // half index o > 0 is full index CENTRE + o
+    dx = f % St::W - M;
+    dy = (f / St::W) % St::W - M;
+    dz = f / (St::W * St::W) - M;
 }
 
 __device__ __forceinline__ int wrap_axis(int c, int d, int nc, int &k)
@@ -301,18 +308,18 @@ __device__ __forceinline__ void load_i(const DevModel &m, const float4 *com, con
             I.e[a] = (SIG::role(a, m) & AX_ROLES) ? make_float4(sa * u.x, sa * u.y, sa * u.z, 0.f)
                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int a = 0; a < SIG::S; a++) {
-        I.d[a][0] = I.d[a][1] = I.d[a][2] = 0.f;
-        I.e[a] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (!SIG::SINGLE && SIG::role(a, m)) {
-            const float4 t4 = geo[(long long)si * K + a];
-            I.d[a][0] = t4.x;
-            I.d[a][1] = t4.y;
-            I.d[a][2] = t4.z;
-            if (SIG::role(a, m) & AX_ROLES) I.e[a] = geo[(long long)si * K + SIG::s_of(m) + SIG::slot(a, m)];
+        for (int a = 0; a < SIG::S; a++) {
+            I.d[a][0] = I.d[a][1] = I.d[a][2] = 0.f;
+            I.e[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!SIG::SINGLE && SIG::role(a, m)) {
+                const float4 t4 = geo[(long long)si * K + a];
+                I.d[a][0] = t4.x;
+                I.d[a][1] = t4.y;
+                I.d[a][2] = t4.z;
+                if (SIG::role(a, m) & AX_ROLES) I.e[a] = geo[(long long)si * K + SIG::s_of(m) + SIG::slot(a, m)];
+            }
         }
     }
 }
@@ -480,6 +487,13 @@ constexpr int JCAP = MD_JCAP;  // staged candidates per segment (a multiple of 3
 constexpr int NTEST = MD_TEST_UNROLL;   // candidates per lane per test round
 constexpr int QCAP = 32 * (NTEST + 1);  // hit queue (31 waiting + NTEST x 32 new)
 
+// Stencils wider than a warp (M = 2): each stencil cell's first slot and
+// the exclusive prefix of the counts, per warp in shared memory.
+struct StencilMeta {
+    int j0[Stencil<2>::FULL];
+    int pre[Stencil<2>::FULL + 1];
+};
+
 // Per-warp staging area; Extra is the pair operation's own shared state.
 template <class Extra>
 struct WarpTile {
@@ -539,49 +553,90 @@ __device__ __forceinline__ void for_each_cell(long long ncell, unsigned *ctr, in
 //                                     their k are distinct)
 //   count_examined(n)
 // cell_start holds global slots; c is the cell index inside the grid.
-template <class SIG, bool HALF, class Op, class Extra>
+template <class SIG, bool HALF, int M = 1, class Op, class Extra>
 __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView &g, const int *__restrict__ cell_start,
                                               const float4 *__restrict__ com, const float4 *__restrict__ geo,
                                               const double *__restrict__ r64, int K, long long c, WarpTile<Extra> &T,
-                                              Op &op, int lane)
+                                              Op &op, int lane, StencilMeta *meta = nullptr)
 {
     constexpr int IMAX = Op::IMAX;
     static_assert(IMAX <= 32 && JCAP <= 65536, "queue entry packs (i << 16) | k");
     const unsigned lt_mask = (1u << lane) - 1u;
-    constexpr int NOFF = HALF ? 14 : 27;
-    constexpr int SELF = HALF ? 0 : 13;  // stencil index of the cell itself
+    static_assert(M == 1 || M == 2, "stencil radius 1 or 2 cells");
+    constexpr int NOFF = HALF ? Stencil<M>::HALFN : Stencil<M>::FULL;
+    constexpr int SELF = HALF ? 0 : Stencil<M>::CENTRE;  // stencil index of the cell itself
     const int cx = (int)(c % g.nc[0]);
     const int cy = (int)((c / g.nc[0]) % g.nc[1]);
     const int cz = (int)(c / ((long long)g.nc[0] * g.nc[1]));
-    // stencil cell of lane t (< NOFF): first slot, count, image offset and
-    // the exclusive prefix of the counts (position in the concatenated
-    // candidate list); loaded at once, then read by shuffles while staging
-    int t_j0 = 0, t_cnt = 0;
+    // M = 1: stencil cell of lane t (< NOFF): first slot, count, offset of
+    // its cell centre and the exclusive prefix of the counts (position in the
+    // concatenated candidate list); loaded at once, then read by shuffles
+    // while staging.  M = 2 (more stencil cells than lanes): first slots and
+    // prefixes in shared memory, offsets recomputed from the stencil index.
+    int t_j0 = 0, t_cnt = 0, t_pre = 0;
     float t_ox = 0.f, t_oy = 0.f, t_oz = 0.f;
-    if (lane < NOFF) {
-        int dx, dy, dz, kx, ky, kz;
-        stencil_offset(HALF, lane, dx, dy, dz);
-        const int nx = wrap_axis(cx, dx, g.nc[0], kx);
-        const int ny = wrap_axis(cy, dy, g.nc[1], ky);
-        const int nz = wrap_axis(cz, dz, g.nc[2], kz);
-        const long long cn = g.cell0 + ((long long)nz * g.nc[1] + ny) * g.nc[0] + nx;
-        t_j0 = cell_start[cn];
-        t_cnt = cell_start[cn + 1] - t_j0;
-        t_ox = dx * g.ellf[0];
-        t_oy = dy * g.ellf[1];
-        t_oz = dz * g.ellf[2];
-    }
-    int t_pre = t_cnt;  // inclusive scan, then exclusive
+    int n_cand, self_pre, self_cnt, s0;
+    if constexpr (M == 1) {
+        if (lane < NOFF) {
+            int dx, dy, dz, kx, ky, kz;
+            stencil_offset<M>(HALF, lane, dx, dy, dz);
+            const int nx = wrap_axis(cx, dx, g.nc[0], kx);
+            const int ny = wrap_axis(cy, dy, g.nc[1], ky);
+            const int nz = wrap_axis(cz, dz, g.nc[2], kz);
+            const long long cn = g.cell0 + ((long long)nz * g.nc[1] + ny) * g.nc[0] + nx;
+            t_j0 = cell_start[cn];
+            t_cnt = cell_start[cn + 1] - t_j0;
+            t_ox = dx * g.ellf[0];
+            t_oy = dy * g.ellf[1];
+            t_oz = dz * g.ellf[2];
+        }
+        t_pre = t_cnt;  // inclusive scan, then exclusive
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(FULLMASK, t_pre, o);
-        if (lane >= o) t_pre += v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULLMASK, t_pre, o);
+            if (lane >= o) t_pre += v;
+        }
+        n_cand = __shfl_sync(FULLMASK, t_pre, NOFF - 1);
+        t_pre -= t_cnt;
+        self_pre = __shfl_sync(FULLMASK, t_pre, SELF);
+        self_cnt = __shfl_sync(FULLMASK, t_cnt, SELF);
+        // the i-cell is the stencil's own entry (no separate load round)
+        s0 = __shfl_sync(FULLMASK, t_j0, SELF);
+    } else {
+        int carry = 0;
+        for (int e0 = 0; e0 < NOFF; e0 += 32) {  // warp-uniform
+            const int e = e0 + lane;
+            int j0 = 0, cnt = 0;
+            if (e < NOFF) {
+                int dx, dy, dz, kx, ky, kz;
+                stencil_offset<M>(HALF, e, dx, dy, dz);
+                const int nx = wrap_axis(cx, dx, g.nc[0], kx);
+                const int ny = wrap_axis(cy, dy, g.nc[1], ky);
+                const int nz = wrap_axis(cz, dz, g.nc[2], kz);
+                const long long cn = g.cell0 + ((long long)nz * g.nc[1] + ny) * g.nc[0] + nx;
+                j0 = cell_start[cn];
+                cnt = cell_start[cn + 1] - j0;
+            }
+            int inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULLMASK, inc, o);
+                if (lane >= o) inc += v;
+            }
+            if (e < NOFF) {
+                meta->j0[e] = j0;
+                meta->pre[e] = carry + inc - cnt;
+            }
+            carry += __shfl_sync(FULLMASK, inc, 31);
+        }
+        if (lane == 0) meta->pre[NOFF] = carry;
+        __syncwarp();
+        n_cand = carry;
+        self_pre = meta->pre[SELF];
+        self_cnt = meta->pre[SELF + 1] - self_pre;
+        s0 = meta->j0[SELF];
     }
-    const int n_cand = __shfl_sync(FULLMASK, t_pre, NOFF - 1);
-    t_pre -= t_cnt;
-    const int self_pre = __shfl_sync(FULLMASK, t_pre, SELF), self_cnt = __shfl_sync(FULLMASK, t_cnt, SELF);
-    // the i-cell is the stencil's own entry (no separate load round)
-    const int s0 = __shfl_sync(FULLMASK, t_j0, SELF), n_i = self_cnt;
+    const int n_i = self_cnt;
     if (n_i == 0) return;
     for (int ig = 0; ig < n_i; ig += IMAX) {
         const int ni = min(IMAX, n_i - ig);
@@ -608,24 +663,45 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
             const int nj = min(JCAP, n_cand - seg0);
             // every lane stages entries x = seg0 + lane + 32 b; its stencil
             // cell is the last one whose prefix is <= x (binary search over
-            // the lanes' prefixes); the loads of all rounds are independent
+            // the lanes' prefixes for M = 1, over the shared prefixes for
+            // M = 2); the loads of all rounds are independent
+            if constexpr (M == 1) {
 #pragma unroll 4
-            for (int tb = 0; tb < nj; tb += 32) {  // warp-uniform trip count: the shuffles need every lane
-                const int t = tb + lane;
-                const int x = seg0 + t;
-                int o = 0;
+                for (int tb = 0; tb < nj; tb += 32) {  // warp-uniform trip count: the shuffles need every lane
+                    const int t = tb + lane;
+                    const int x = seg0 + t;
+                    int o = 0;
 #pragma unroll
-                for (int st = 16; st > 0; st >>= 1) {
-                    const int c2 = o + st;
-                    const int p2 = __shfl_sync(FULLMASK, t_pre, c2 < NOFF ? c2 : 0);
-                    if (c2 < NOFF && p2 <= x) o = c2;
+                    for (int st = 16; st > 0; st >>= 1) {
+                        const int c2 = o + st;
+                        const int p2 = __shfl_sync(FULLMASK, t_pre, c2 < NOFF ? c2 : 0);
+                        if (c2 < NOFF && p2 <= x) o = c2;
+                    }
+                    const int js = __shfl_sync(FULLMASK, t_j0, o) + (x - __shfl_sync(FULLMASK, t_pre, o));
+                    const float ox = __shfl_sync(FULLMASK, t_ox, o), oy = __shfl_sync(FULLMASK, t_oy, o),
+                                oz = __shfl_sync(FULLMASK, t_oz, o);
+                    if (t < nj) {
+                        const float4 cj = com[js];
+                        T.jc[t] = make_float4(cj.x + ox, cj.y + oy, cj.z + oz, __int_as_float(js));
+                        T.jst[t] = (unsigned char)o;
+                    }
                 }
-                const int js = __shfl_sync(FULLMASK, t_j0, o) + (x - __shfl_sync(FULLMASK, t_pre, o));
-                const float ox = __shfl_sync(FULLMASK, t_ox, o), oy = __shfl_sync(FULLMASK, t_oy, o),
-                            oz = __shfl_sync(FULLMASK, t_oz, o);
-                if (t < nj) {
+            } else {
+#pragma unroll 2
+                for (int t = lane; t < nj; t += 32) {
+                    const int x = seg0 + t;
+                    int o = 0;  // the last stencil cell whose prefix is <= x (an occupied one)
+#pragma unroll
+                    for (int st = 64; st > 0; st >>= 1) {
+                        const int c2 = o + st;
+                        if (c2 < NOFF && meta->pre[c2] <= x) o = c2;
+                    }
+                    int dx, dy, dz;
+                    stencil_offset<M>(HALF, o, dx, dy, dz);
+                    const int js = meta->j0[o] + (x - meta->pre[o]);
                     const float4 cj = com[js];
-                    T.jc[t] = make_float4(cj.x + ox, cj.y + oy, cj.z + oz, __int_as_float(js));
+                    T.jc[t] = make_float4(cj.x + dx * g.ellf[0], cj.y + dy * g.ellf[1], cj.z + dz * g.ellf[2],
+                                          __int_as_float(js));
                     T.jst[t] = (unsigned char)o;
                 }
             }
@@ -652,7 +728,7 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
                 // the same test in FP64 from the FP64 state (pairs near the cut-off)
                 auto test64 = [&](int k) -> bool {
                     int dx, dy, dz, kx, ky, kz;
-                    stencil_offset(HALF, T.jst[k], dx, dy, dz);
+                    stencil_offset<M>(HALF, T.jst[k], dx, dy, dz);
                     wrap_axis(cx, dx, g.nc[0], kx);
                     wrap_axis(cy, dy, g.nc[1], ky);
                     wrap_axis(cz, dz, g.nc[2], kz);

@@ -40,7 +40,7 @@ class md_site_types(C.Structure):
 
 class md_options(C.Structure):
     _fields_ = [("eps_rf", C.c_double), ("lj_shift", C.c_int32), ("lj_lrc", C.c_int32),
-                ("deterministic", C.c_int32), ("half_shell", C.c_int32)]
+                ("deterministic", C.c_int32), ("half_shell", C.c_int32), ("cell_div", C.c_int32)]
 
 
 class md_observables(C.Structure):
@@ -228,11 +228,12 @@ class Model:
 
 
 # ------------------------------------------------------- C-ABI functions
-def md_create(box, cutoff, model: dict, eps_rf=math.inf, lj_shift=0, lj_lrc=0, deterministic=1, half_shell=0):
+def md_create(box, cutoff, model: dict, eps_rf=math.inf, lj_shift=0, lj_lrc=0, deterministic=1, half_shell=0,
+              cell_div=1):
     """Returns (handle, Model) -- keep the Model alive with the handle."""
     M = Model(model)
     b = (C.c_double * 3)(*[float(x) for x in box])
-    o = md_options(float(eps_rf), int(lj_shift), int(lj_lrc), int(deterministic), int(half_shell))
+    o = md_options(float(eps_rf), int(lj_shift), int(lj_lrc), int(deterministic), int(half_shell), int(cell_div))
     h = C.c_void_p()
     _check(lib().md_create(b, float(cutoff), C.byref(M.types), C.byref(o), C.byref(h)))
     return h, M
@@ -349,10 +350,11 @@ def md_destroy(h):
 class System:
     """Owning wrapper: one md_system handle plus its model structs."""
 
-    def __init__(self, cfg: dict, deterministic=1, half_shell=0):
+    def __init__(self, cfg: dict, deterministic=1, half_shell=0, cell_div=1):
         self.cfg = cfg
         self.h, self._model = md_create(cfg["box"], cfg["rc"], cfg["model"], cfg.get("eps_rf", math.inf),
-                                        cfg.get("lj_shift", 0), cfg.get("lj_lrc", 0), deterministic, half_shell)
+                                        cfg.get("lj_shift", 0), cfg.get("lj_lrc", 0), deterministic, half_shell,
+                                        cell_div)
 
     def set(self, r, q, v=None, j=None, stream=None):
         md_set_molecules(self.h, r, q, v, j, stream)

@@ -1,5 +1,6 @@
 """C-ABI library: loads, exports every declared symbol, and validates its
 arguments on the host before touching the GPU (CPU only, no compute)."""
+import ctypes as C
 import math
 import os
 import re
@@ -57,7 +58,7 @@ def test_box_smaller_than_two_cutoffs_is_rejected():
 
 @pytest.mark.parametrize("bad", [
     dict(rc=-1.0), dict(rc=float("nan")), dict(box=(10.0, float("inf"), 10.0)),
-    dict(eps_rf=0.5), dict(eps_rf=float("nan")),
+    dict(eps_rf=0.5), dict(eps_rf=float("nan")), dict(cell_div=3), dict(cell_div=-1),
 ])
 def test_bad_scalars_are_rejected(bad):
     with pytest.raises(md.MDError) as e:
@@ -86,6 +87,18 @@ def test_bad_models_are_rejected():
     with pytest.raises(md.MDError) as e:
         _create(model=m)
     assert e.value.code == -9  # more merged sites than supported
+
+
+def test_batch_rejects_half_cutoff_cells():
+    """Replicas use cells of edge >= cutoff: cell_div = 2 is refused before
+    anything is allocated."""
+    M = md.Model(mdgen.model_lj())
+    boxes = (C.c_double * 6)(10.0, 10.0, 10.0, 12.0, 12.0, 12.0)
+    h = C.c_void_p()
+    for div, code in ((2, -9), (3, -1)):
+        o = md.md_options(math.inf, 0, 0, 0, 1, div)
+        assert md.lib().md_batch_create(2, boxes, 2.5, C.byref(M.types), C.byref(o), C.byref(h)) == code
+        assert not h.value
 
 
 def test_null_handle_calls_fail_cleanly():

@@ -36,8 +36,8 @@ def _log(**kw):
             f.write(json.dumps(kw) + "\n")
 
 
-def gpu_eval(cfg, deterministic=1, half=0, device=True):
-    s = md.System(cfg, deterministic=deterministic, half_shell=half)
+def gpu_eval(cfg, deterministic=1, half=0, device=True, cell_div=1):
+    s = md.System(cfg, deterministic=deterministic, half_shell=half, cell_div=cell_div)
     if device:
         d = torch.device("cuda:0")
         t = {k: torch.from_numpy(np.ascontiguousarray(cfg[k])).to(d) for k in ("r", "v", "q", "j")}
@@ -123,6 +123,83 @@ def test_full_shell_cells_from_counter(name):
     Fd, taud, obsd = gpu_eval(cfg, deterministic=1, half=0)
     assert np.array_equal(F, Fd) and np.array_equal(tau, taud)
     assert obs["n_mol_pairs"] == obsd["n_mol_pairs"] and obs["n_examined"] == obsd["n_examined"]
+
+
+# ------------------------------------------- cells of edge r_c / 2 (§3)
+def _examined_pairs(r, box, rc, m):
+    """Unordered molecule pairs whose cells (floor(m L / r_c) per axis, the
+    cell of x is floor(x / edge)) are at most m cells apart along every axis,
+    periodically: the pairs a stencil of radius m examines when every axis
+    has at least 2m + 1 cells."""
+    L = np.asarray(box, dtype=float)
+    nc = np.floor(L * m / (rc * (1.0 + 1e-9))).astype(np.int64)
+    iell = 1.0 / (L / nc)
+    c = np.clip(np.floor(r * iell).astype(np.int64), 0, nc - 1)
+    n, tot = len(r), 0
+    for i0 in range(0, n, 128):
+        d = np.abs(c[i0:i0 + 128, None, :] - c[None, :, :])
+        d = np.minimum(d, nc - d)
+        ok = (d <= m).all(axis=2) & (np.arange(n)[None, :] > np.arange(i0, min(i0 + 128, n))[:, None])
+        tot += int(ok.sum())
+    return tot
+
+
+HALF_CELL_CASES = ["lj-4096", "lj-ragged-1999", "2cljq-20000", "2cljdq-3000", "2cljdq-smallbox-500",
+                   "2cljdq-dilute-700", "4site-6000", "slab-60000", "2cljq-dense-cells-8000"]
+
+
+@pytest.mark.parametrize("half", [0, 1])
+@pytest.mark.parametrize("name", HALF_CELL_CASES)
+def test_force_parity_half_cutoff_cells(name, half):
+    """cell_div = 2 (§3 smaller cells: edge >= r_c / 2, the 125-cell
+    stencil): the same interacting pairs and results as the oracle, and the
+    examined pairs are exactly those of the smaller stencil."""
+    cfg = CASES[name]()
+    Fo, to, oo = oracle_eval(cfg)
+    F, tau, obs = gpu_eval(cfg, deterministic=1 - half, half=half, cell_div=2)
+    check_parity(f"{name}/div2/half{half}", cfg, F, tau, obs, Fo, to, oo, exact_examined=False)
+    ncs = [int(math.floor(2 * L / (cfg["rc"] * (1 + 1e-9)))) for L in cfg["box"]]
+    if min(ncs) >= 5 and len(F) <= 20000:
+        assert obs["n_examined"] == _examined_pairs(cfg["r"], cfg["box"], cfg["rc"], 2)
+    assert obs["n_examined"] <= oo["n_examined"]  # equal when one stencil already covers the box
+
+
+def test_half_cutoff_cells_hit_fraction_matches_paper():
+    """§3: cells of edge r_c examine 27 r_c^3 around a molecule and ~16% of
+    the computed distances of a homogeneous configuration are inside r_c;
+    cells of edge r_c / 2 examine 15.6 r_c^3 and ~27% are.  Homogeneous here:
+    seeded uniform positions (a lattice commensurate with the cells would
+    bias the examined count) in a box of 15 cut-off lengths, so both cell
+    sizes divide it exactly."""
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
+    L = 15 * 2.5 * (1 + 1e-8)
+    n = int(0.6 * L ** 3)
+    cfg = mdgen.config_lj_fluid(n=n)
+    assert cfg["rc"] == 2.5
+    cfg["box"] = (L, L, L)
+    cfg["r"] = np.random.default_rng(1408_0007).uniform(0.0, L, size=(n, 3))
+    frac = {}
+    for div in (1, 2):
+        _, _, obs = gpu_eval(cfg, deterministic=0, half=1, cell_div=div)
+        frac[div] = obs["n_mol_pairs"] / obs["n_examined"]
+    assert frac[1] == pytest.approx(g["hit_fraction_rc_cells"]["value"], abs=0.01)
+    assert frac[2] == pytest.approx(g["hit_fraction_half_rc_cells"]["value"], abs=0.01)
+    assert frac[2] == pytest.approx((4 * math.pi / 3) / g["half_cell_volume_rc3"]["value"], rel=0.03)
+
+
+@pytest.mark.parametrize("half", [0, 1])
+def test_trajectory_half_cutoff_cells(half):
+    _traj_compare(mdgen.config_2cljq(n=4000), 20, 1e-5, half=half, cell_div=2)
+    _traj_compare(mdgen.config_lj_fluid(n=4096), 50, 1e-5, T_target=0.8, half=half, cell_div=2)
+
+
+def test_param_grad_refuses_half_cutoff_cells():
+    cfg = mdgen.config_4site(n=2000)
+    s = md.System(cfg, cell_div=2)
+    with pytest.raises(md.MDError) as e:
+        s.param_grad(cfg["r"][None], cfg["q"][None])
+    assert e.value.code == -9
+    s.close()
 
 
 def test_full_shell_is_deterministic():
@@ -233,8 +310,8 @@ def test_nonfinite_input_rejected_on_host():
 
 
 # ----------------------------------------------------------- trajectories
-def _traj_compare(cfg, n_steps, tol, T_target=0.0, half=0):
-    s = md.System(cfg, deterministic=1 - half, half_shell=half)
+def _traj_compare(cfg, n_steps, tol, T_target=0.0, half=0, cell_div=1):
+    s = md.System(cfg, deterministic=1 - half, half_shell=half, cell_div=cell_div)
     s.set(cfg["r"], cfg["q"], cfg["v"], cfg["j"])
     s.step(n_steps, cfg["dt"], T_target=T_target)
     r, v, q, j = s.molecules()
