@@ -44,6 +44,7 @@ def flops_per_pair():
     return int(re.search(r"#define MD_FLOPS_PAIR_2CLJQ (\d+)", txt).group(1))
 
 
+WORKLOAD_2CLJQ = "2CLJQ rigid-molecule fluid N=262144 rho=0.55 T=1 rc=3 dt=0.001 (one md step)"
 FORCE_SOURCES = ("md_force.cu", "md_force.cuh", "md_forceop.cuh", "md_internal.cuh", "md_pair.cuh")
 
 
@@ -160,8 +161,7 @@ def run_reference(args, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded 2CLJQ fluid)",
-            "config": {"workload": "2CLJQ rigid-molecule fluid N=262144 rho=0.55 T=1 rc=3 (one md step)",
-                       "l2": "n/a (CPU)"},
+            "config": {"workload": WORKLOAD_2CLJQ, "l2": "n/a (CPU)", "parallelism": f"{cores} host cores"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} full oracle leapfrog steps (linked cells, all cores)"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -302,7 +302,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 site math, f64 accumulation/state",
             "data": "synthetic (seeded 2CLJQ fluid, random orientations)",
-            "config": {"workload": "2CLJQ rigid-molecule fluid N=262144 rho=0.55 T=1 rc=3 dt=0.001 (one md step)",
+            "config": {"workload": WORKLOAD_2CLJQ,
                        "shell": args.shell, "cells_per_cutoff": args.cell_div,
                        "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
