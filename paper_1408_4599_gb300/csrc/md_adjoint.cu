@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(MD_WARPS * 32) k_adjoint(const __grid_constant
     gv.bandf = A.g.bandf;
     gv.cell0 = 0;
     Op op(m, A, K);
-    for_each_cell(A.g.ncell, A.cell_ctr, warp, lane, [&](long long c) {
+    for_each_cell(A.g.ncell, 1, A.cell_ctr, warp, lane, [&](long long c, int) {
         traverse_cell<SIG, HALF>(m, gv, A.cell_start, A.com, A.geo, A.r, K, c, *T, op, lane);
     });
     __shared__ float s_red[MD_WARPS][LY::NACC];

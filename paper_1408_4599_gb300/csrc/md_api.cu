@@ -669,8 +669,10 @@ md_status md_create(const double box[3], double cutoff, const md_site_types *typ
     s->half_eff = (opt.half_shell && !opt.deterministic && g.nc[0] >= nmin && g.nc[1] >= nmin && g.nc[2] >= nmin) ? 1 : 0;
     s->d.K = s->m.single_lj_at_com ? 0 : (s->m.linear ? 1 : s->m.S + s->m.NA);
 
-    long long fb = (ncell + MD_WARPS - 1) / MD_WARPS;
-    s->n_force_blocks = (int)(fb < force_blocks_default() ? fb : force_blocks_default());  // upper bound of the grid
+    // upper bound of the force grid: one block per MD_WARPS units of work, a
+    // cell being split into up to 4 units in small systems
+    long long fb = (4 * ncell + MD_WARPS - 1) / MD_WARPS;
+    s->n_force_blocks = (int)(fb < force_blocks_default() ? fb : force_blocks_default());
     s->n_kin_blocks = 152 * 4;
     DevState &d = s->d;
     cudaError_t e = cudaMalloc((void **)&d.cell_count, sizeof(int) * ncell);

@@ -409,6 +409,7 @@ BatchArgs batch_args(md_batch *b, bool half_list)
     B.f.flags = b->d.flags;
     B.f.to_acc = 1;
     B.f.cell_ctr = nullptr;
+    B.f.parts = 1;
     B.grids = b->dgrids;
     B.rep_of_cell = b->rep_of_cell;
     B.work = half_list ? b->work : b->work + b->n_work_half;

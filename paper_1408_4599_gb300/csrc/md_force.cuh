@@ -69,9 +69,15 @@ __global__ void __launch_bounds__(MD_WARPS * 32, force_min_blocks<SIG>()) k_forc
     gv.bandf = A.g.bandf;
     gv.cell0 = 0;
     Op op(m, A, K, T);
-    for_each_cell(A.g.ncell, A.cell_ctr, warp, lane, [&](long long c) {
-        traverse_cell<SIG, HALF, M>(m, gv, A.cell_start, A.com, A.geo, A.r, K, c, *T, op, lane, meta);
-    });
+    if (A.parts > 1) {
+        for_each_cell(A.g.ncell, A.parts, A.cell_ctr, warp, lane, [&](long long c, int p) {
+            traverse_cell<SIG, HALF, M>(m, gv, A.cell_start, A.com, A.geo, A.r, K, c, *T, op, lane, meta, p, A.parts);
+        });
+    } else {  // whole cells: the traversal with a constant share (the common case, kept free of the split)
+        for_each_cell(A.g.ncell, 1, A.cell_ctr, warp, lane, [&](long long c, int) {
+            traverse_cell<SIG, HALF, M>(m, gv, A.cell_start, A.com, A.geo, A.r, K, c, *T, op, lane, meta);
+        });
+    }
 
     // block partials: FP32 warp sums of the compensated lane sums; FP64 only
     // once per value per block
@@ -113,7 +119,12 @@ struct LaunchForce {
         return run<SIG, false>();
     }
     // persistent grid: as many blocks as can be resident, never more than
-    // the cells need nor than the partials hold
+    // the units of work need nor than the partials hold.  With cells handed
+    // out from the counter and fewer than half as many cells as resident
+    // warps (small systems), each cell's i molecules are split into up to
+    // MAX_PARTS units so that more warps share the work; deterministic runs
+    // keep one unit per cell (the split changes the FP32 summation grouping).
+    static constexpr int MAX_PARTS = 4;
     template <class SIG, bool HALF>
     cudaError_t run() const
     {
@@ -124,11 +135,17 @@ struct LaunchForce {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<SIG, HALF, M>, MD_WARPS * 32, sm);
         long long want = (long long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-        const long long need = (A.g.ncell + MD_WARPS - 1) / MD_WARPS;
+        ForceArgs B = A;
+        B.parts = 1;
+        if (B.cell_ctr && A.g.ncell > 0) {
+            const long long p = 2 * want * MD_WARPS / A.g.ncell;
+            B.parts = (int)(p < 1 ? 1 : (p > MAX_PARTS ? MAX_PARTS : p));
+        }
+        const long long need = (A.g.ncell * B.parts + MD_WARPS - 1) / MD_WARPS;
         if (want > need) want = need;
         if (want > n_blocks) want = n_blocks;
         if (want < 1) want = 1;
-        k_force<SIG, HALF, M><<<(unsigned)want, MD_WARPS * 32, sm, s>>>(A);
+        k_force<SIG, HALF, M><<<(unsigned)want, MD_WARPS * 32, sm, s>>>(B);
         return cudaGetLastError();
     }
 };

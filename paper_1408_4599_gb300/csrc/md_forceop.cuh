@@ -21,6 +21,7 @@ struct ForceArgs {
     int *flags;
     int to_acc;       // full shell: also accumulate into acc (batched replicas of mixed shells)
     unsigned *cell_ctr;  // non-null: cells are handed out one at a time from this counter
+    int parts;           // each cell's i molecules split into this many units of work
 };
 
 template <bool HALF>

@@ -513,32 +513,37 @@ struct GridView {
     long long cell0;          // first global cell index of this grid
 };
 
-// Calls visit(c) once for every cell c < ncell, each cell by one warp of
-// the grid (warp = the warp's index in its block).  ctr non-null: cells
-// one at a time in counter order, the next claimed when the warp has
-// finished its cell (cell costs vary with the occupation, so warps that
-// finish early take more; claiming ahead balances the tail one cell later
-// and measured slower).  ctr null: a fixed grid stride, the same cells per
-// warp on every launch (fixed summation grouping of the block partials).
+// Calls visit(c, p) once for every part p < parts of every cell c < ncell,
+// each (cell, part) unit by one warp of the grid (warp = the warp's index
+// in its block); a part is a contiguous share of the cell's i molecules.
+// ctr non-null: units one at a time in counter order (the parts of a cell
+// consecutively), the next claimed when the warp has finished its unit
+// (cell costs vary with the occupation, so warps that finish early take
+// more; claiming ahead balances the tail one unit later and measured
+// slower).  ctr null: a fixed grid stride, the same units per warp on every
+// launch (fixed summation grouping of the block partials).
 template <class Visit>
-__device__ __forceinline__ void for_each_cell(long long ncell, unsigned *ctr, int warp, int lane, Visit &&visit)
+__device__ __forceinline__ void for_each_cell(long long ncell, int parts, unsigned *ctr, int warp, int lane,
+                                              Visit &&visit)
 {
+    const long long units = ncell * parts;
     if (ctr) {
         for (;;) {
-            unsigned c = 0;
-            if (lane == 0) c = atomicAdd(ctr, 1u);
-            c = __shfl_sync(FULLMASK, c, 0);
-            if (c >= ncell) break;
-            visit((long long)c);
+            unsigned u = 0;
+            if (lane == 0) u = atomicAdd(ctr, 1u);
+            u = __shfl_sync(FULLMASK, u, 0);
+            if (u >= units) break;
+            visit((long long)(u / parts), (int)(u % parts));
         }
     } else {
-        for (long long c = (long long)blockIdx.x * MD_WARPS + warp; c < ncell; c += (long long)gridDim.x * MD_WARPS)
-            visit(c);
+        for (long long u = (long long)blockIdx.x * MD_WARPS + warp; u < units; u += (long long)gridDim.x * MD_WARPS)
+            visit(u / parts, (int)(u % parts));
     }
 }
 
 // Visits every interacting pair (i in cell c, j in the stencil) in chunks
-// of <= 32 pairs.  The hits of consecutive i molecules of a pass share a
+// of <= 32 pairs; with parts > 1 only the i of share `part` of the cell's
+// molecules.  The hits of consecutive i molecules of a pass share a
 // queue, so a chunk may hold pairs of several i's (contiguous lanes per i,
 // in i order) and only the last chunk of a segment is partly filled.
 // Op provides:
@@ -557,7 +562,8 @@ template <class SIG, bool HALF, int M = 1, class Op, class Extra>
 __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView &g, const int *__restrict__ cell_start,
                                               const float4 *__restrict__ com, const float4 *__restrict__ geo,
                                               const double *__restrict__ r64, int K, long long c, WarpTile<Extra> &T,
-                                              Op &op, int lane, StencilMeta *meta = nullptr)
+                                              Op &op, int lane, StencilMeta *meta = nullptr, int part = 0,
+                                              int parts = 1)
 {
     constexpr int IMAX = Op::IMAX;
     static_assert(IMAX <= 32 && JCAP <= 65536, "queue entry packs (i << 16) | k");
@@ -637,9 +643,11 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
         s0 = meta->j0[SELF];
     }
     const int n_i = self_cnt;
-    if (n_i == 0) return;
-    for (int ig = 0; ig < n_i; ig += IMAX) {
-        const int ni = min(IMAX, n_i - ig);
+    // this unit's share of the cell's i molecules
+    const int i_lo = n_i * part / parts, i_hi = n_i * (part + 1) / parts;  // n_i * parts << 2^31
+    if (i_lo >= i_hi) return;
+    for (int ig = i_lo; ig < i_hi; ig += IMAX) {
+        const int ni = min(IMAX, i_hi - ig);
         op.pass_begin(ig, ni, lane);
         // the first nq queue entries as one chunk (all lanes call)
         auto chunk = [&](int nq) {

@@ -112,16 +112,19 @@ def test_force_parity(name, half):
 @pytest.mark.parametrize("name", ["2cljq-20000", "4site-6000", "lj-dense-cells-12000"])
 def test_full_shell_cells_from_counter(name):
     """Full shell with `deterministic` off: the force kernel takes cells from
-    a counter instead of a fixed grid stride.  Each molecule's force and
-    torque are still summed by the one warp that owns its cell, in a fixed
-    order, so they equal the deterministic run's bitwise; the energy and
-    virial partials group differently and meet the oracle tolerance."""
+    a counter instead of a fixed grid stride, and in these small systems
+    (fewer cells than half the resident warps) splits each cell's i
+    molecules into several units of work.  Forces and torques meet the
+    oracle tolerance and agree with the deterministic run (one unit per
+    cell) up to FP32 summation order; the pair counts are identical."""
     cfg = CASES[name]()
     Fo, to, oo = oracle_eval(cfg)
     F, tau, obs = gpu_eval(cfg, deterministic=0, half=0)
     check_parity(f"{name}/counter", cfg, F, tau, obs, Fo, to, oo, exact_examined=True)
     Fd, taud, obsd = gpu_eval(cfg, deterministic=1, half=0)
-    assert np.array_equal(F, Fd) and np.array_equal(tau, taud)
+    assert np.median(rel_err(F, Fd)) <= 1e-6 and rel_err(F, Fd).max() <= 1e-4
+    if np.abs(taud).max() > 0:
+        assert np.median(rel_err(tau, taud)) <= 1e-6 and rel_err(tau, taud).max() <= 1e-4
     assert obs["n_mol_pairs"] == obsd["n_mol_pairs"] and obs["n_examined"] == obsd["n_examined"]
 
 
