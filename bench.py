@@ -45,7 +45,7 @@ def flops_per_pair():
 
 
 WORKLOAD_2CLJQ = "2CLJQ rigid-molecule fluid N=262144 rho=0.55 T=1 rc=3 dt=0.001 (one md step)"
-FORCE_SOURCES = ("md_force.cu", "md_force.cuh", "md_forceop.cuh", "md_internal.cuh", "md_pair.cuh")
+FORCE_SOURCES = ("md_force.cu", "md_force.cuh", "md_force_inst.cu", "md_forceop.cuh", "md_internal.cuh", "md_pair.cuh")
 
 
 def force_traffic():

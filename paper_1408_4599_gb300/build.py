@@ -1,7 +1,8 @@
 """Builds libmdgpu.so (the C-ABI CUDA library) in-tree for sm_103a.
 
-Each translation unit in ``csrc/`` is compiled in parallel with nvcc into
-``_build/``, then linked into ``paper_1408_4599_gb300/libmdgpu.so``.  The
+Each translation unit in ``csrc/`` (the force kernel's instantiation file
+once per signature and stencil radius) is compiled in parallel with nvcc
+into ``_build/``, then linked into ``paper_1408_4599_gb300/libmdgpu.so``.  The
 compiled objects are not tracked by git.
 """
 from __future__ import annotations
@@ -29,8 +30,27 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
+# Sources compiled once per variant (one object per set of defines): the
+# force kernel's instantiations, one per compiled signature (the order of
+# dispatch_sig) and stencil radius, so that they compile in parallel.
+VARIANTS = {
+    "md_force_inst.cu": [(f"s{sig}m{m}", [f"-DMD_FORCE_SIG={sig}", f"-DMD_FORCE_M={m}"])
+                         for sig in range(6) for m in (1, 2)],
+}
+
+
 def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+
+
+def units():
+    """(source, object, extra nvcc flags) of every object of the library."""
+    out = []
+    for src in sources():
+        base = os.path.basename(src)[:-3]
+        for tag, defs in VARIANTS.get(os.path.basename(src), [("", [])]):
+            out.append((src, os.path.join(BUILD, base + ("_" + tag if tag else "") + ".o"), defs))
+    return out
 
 
 def _deps():
@@ -50,27 +70,30 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    srcs = sources()
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    todo = units()
+    objs = [obj for _, obj, _ in todo]
 
-    def compile_one(src_obj):
-        src, obj = src_obj
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+    def compile_one(unit):
+        src, obj, defs = unit
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *defs, "-c", src, "-o", obj]
         if ptxas_info:
             cmd.insert(1, "-Xptxas=-v")
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
-            raise RuntimeError(f"nvcc failed for {src}:\n{p.stderr}")
+            raise RuntimeError(f"nvcc failed for {src} {' '.join(defs)}:\n{p.stderr}")
         return p.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        logs = list(ex.map(compile_one, zip(srcs, objs)))
+    # the slowest objects first, so that they do not start last
+    order = sorted(todo, key=lambda u: 0 if u[2] else 1)
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(os.cpu_count() or 8, len(order)))) as ex:
+        logs = list(ex.map(compile_one, order))
     if verbose or ptxas_info:
-        for src, log in zip(srcs, logs):
+        for (src, obj, defs), log in zip(order, logs):
             if log.strip():
-                print(f"== {os.path.basename(src)}\n{log}", file=sys.stderr)
+                print(f"== {os.path.basename(obj)}\n{log}", file=sys.stderr)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    # no undefined symbols: a missing instantiation fails here, not at load
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-Xlinker", "--no-undefined"]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stderr}")

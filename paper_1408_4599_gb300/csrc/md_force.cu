@@ -1,11 +1,25 @@
-// md_force.cu -- launches of the linked-cell force kernel (md_force.cuh)
-// for cells of edge >= r_c (27- / 14-cell stencils) and the FP32 -> FP64
+// md_force.cu -- launches of the linked-cell force kernel (md_force.cuh,
+// instantiated by md_force_inst.cu) for cells of edge >= r_c (27- / 14-cell
+// stencils) or >= r_c / 2 (125- / 63-cell stencils), and the FP32 -> FP64
 // finalize of the half-shell accumulators.
-#include "md_force.cuh"
+#include "md_forceop.cuh"
 
 using namespace mdk;
 
 namespace {
+
+// Dispatch target of dispatch_sig: the instantiation for one signature.
+template <int M>
+struct LaunchForce {
+    const ForceArgs &A;
+    int half, n_blocks;
+    cudaStream_t s;
+    template <class SIG>
+    cudaError_t operator()() const
+    {
+        return launch_force_sig<SIG, M>(A, half, n_blocks, s);
+    }
+};
 
 // Half shell: FP32 accumulator records -> FP64 F, tau; non-finite check.
 __global__ void k_force_finalize(const float *acc, long long n, double *F, double *tau, int *flags)
@@ -53,7 +67,7 @@ cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half
         e = cudaMemsetAsync(d.facc, 0, sizeof(float) * FACC_STRIDE * (d.n > 0 ? d.n : 1), s);
         if (e != cudaSuccess) return e;
     }
-    if (g.m == 2) return launch_force_radius2(A, half_shell, n_blocks, s);
+    if (g.m == 2) return dispatch_sig(m, LaunchForce<2>{A, half_shell, n_blocks, s});
     return dispatch_sig(m, LaunchForce<1>{A, half_shell, n_blocks, s});
 }
 

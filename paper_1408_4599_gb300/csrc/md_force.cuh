@@ -25,8 +25,10 @@
 
 #include "md_forceop.cuh"
 
-// Instantiated by md_force.cu (stencil radius 1) and md_force_m2.cu (radius
-// 2), each translation unit with its own copy of this anonymous namespace.
+// Instantiated by md_force_inst.cu, which build.py compiles once per
+// compiled signature and stencil radius (one kernel pair per object, all
+// compiled in parallel); md_force.cu sees only the declaration of
+// launch_force_sig in md_forceop.cuh.
 namespace {
 
 using namespace mdk;
@@ -107,50 +109,47 @@ __global__ void __launch_bounds__(MD_WARPS * 32, force_min_blocks<SIG>()) k_forc
     }
 }
 
-template <int M>
-struct LaunchForce {
-    const ForceArgs &A;
-    int half, n_blocks;
-    cudaStream_t s;
-    template <class SIG>
-    cudaError_t operator()() const
-    {
-        if (half) return run<SIG, true>();
-        return run<SIG, false>();
+// Persistent grid: as many blocks as can be resident, never more than the
+// units of work need nor than the partials hold.  With cells handed out
+// from the counter and fewer than half as many cells as resident warps
+// (small systems), each cell's i molecules are split into up to
+// FORCE_MAX_PARTS units so that more warps share the work; deterministic
+// runs keep one unit per cell (the split changes the FP32 summation
+// grouping).
+constexpr int FORCE_MAX_PARTS = 4;
+
+template <class SIG, bool HALF, int M>
+cudaError_t run_force(const ForceArgs &A, int n_blocks, cudaStream_t s)
+{
+    const size_t sm = force_smem<SIG, HALF, M>();
+    cudaFuncSetAttribute(k_force<SIG, HALF, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<SIG, HALF, M>, MD_WARPS * 32, sm);
+    long long want = (long long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    ForceArgs B = A;
+    B.parts = 1;
+    if (B.cell_ctr && A.g.ncell > 0) {
+        const long long p = 2 * want * MD_WARPS / A.g.ncell;
+        B.parts = (int)(p < 1 ? 1 : (p > FORCE_MAX_PARTS ? FORCE_MAX_PARTS : p));
     }
-    // persistent grid: as many blocks as can be resident, never more than
-    // the units of work need nor than the partials hold.  With cells handed
-    // out from the counter and fewer than half as many cells as resident
-    // warps (small systems), each cell's i molecules are split into up to
-    // MAX_PARTS units so that more warps share the work; deterministic runs
-    // keep one unit per cell (the split changes the FP32 summation grouping).
-    static constexpr int MAX_PARTS = 4;
-    template <class SIG, bool HALF>
-    cudaError_t run() const
-    {
-        const size_t sm = force_smem<SIG, HALF, M>();
-        cudaFuncSetAttribute(k_force<SIG, HALF, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        int per_sm = 0, dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<SIG, HALF, M>, MD_WARPS * 32, sm);
-        long long want = (long long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-        ForceArgs B = A;
-        B.parts = 1;
-        if (B.cell_ctr && A.g.ncell > 0) {
-            const long long p = 2 * want * MD_WARPS / A.g.ncell;
-            B.parts = (int)(p < 1 ? 1 : (p > MAX_PARTS ? MAX_PARTS : p));
-        }
-        const long long need = (A.g.ncell * B.parts + MD_WARPS - 1) / MD_WARPS;
-        if (want > need) want = need;
-        if (want > n_blocks) want = n_blocks;
-        if (want < 1) want = 1;
-        k_force<SIG, HALF, M><<<(unsigned)want, MD_WARPS * 32, sm, s>>>(B);
-        return cudaGetLastError();
-    }
-};
+    const long long need = (A.g.ncell * B.parts + MD_WARPS - 1) / MD_WARPS;
+    if (want > need) want = need;
+    if (want > n_blocks) want = n_blocks;
+    if (want < 1) want = 1;
+    k_force<SIG, HALF, M><<<(unsigned)want, MD_WARPS * 32, sm, s>>>(B);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
-// Launches the force kernel of stencil radius 2 (md_force_m2.cu).
-cudaError_t launch_force_radius2(const mdk::ForceArgs &A, int half_shell, int n_blocks, cudaStream_t s);
+namespace mdk {
+
+template <class SIG, int M>
+cudaError_t launch_force_sig(const ForceArgs &A, int half_shell, int n_blocks, cudaStream_t s)
+{
+    return half_shell ? run_force<SIG, true, M>(A, n_blocks, s) : run_force<SIG, false, M>(A, n_blocks, s);
+}
+
+}  // namespace mdk

@@ -24,6 +24,13 @@ struct ForceArgs {
     int parts;           // each cell's i molecules split into this many units of work
 };
 
+// Launches the single-system force kernel (md_force.cuh) for signature SIG
+// and stencil radius M (1: cells of edge >= r_c, 2: >= r_c / 2), half or
+// full shell.  Defined in md_force.cuh and explicitly instantiated for every
+// compiled signature by md_force_inst.cu.
+template <class SIG, int M>
+cudaError_t launch_force_sig(const ForceArgs &A, int half_shell, int n_blocks, cudaStream_t s);
+
 template <bool HALF>
 struct ForceExtra {
     float4 jf[HALF ? JCAP : 1];  // Newton-3 reactions: F, tau_x

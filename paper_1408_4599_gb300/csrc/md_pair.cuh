@@ -89,6 +89,14 @@ struct SigDyn {
 
 constexpr unsigned TY_4SITE = sigkey(0, 1, 1);  // LJ types of the 4-site model's sites
 
+// The compiled signatures by name.  The two-centre models are compiled for
+// the linear geometry only, their multipole site at the centre of mass.
+using Sig1CLJ = SigStatic<1, ROLE_LJ, true>;
+using Sig2CLJ = SigStatic<2, SIG_2CLJ, false, 0, true>;
+using Sig2CLJQ = SigStatic<3, SIG_2CLJQ, false, 0, true, 4u>;
+using Sig2CLJDQ = SigStatic<3, SIG_2CLJDQ, false, 0, true, 4u>;
+using Sig4Site = SigStatic<5, SIG_4SITE, false, TY_4SITE>;
+
 // Dispatch of a model to its compiled signature: f.template operator()<SIG>().
 template <class F>
 __host__ auto dispatch_sig(const DevModel &m, F &&f)
@@ -98,17 +106,13 @@ __host__ auto dispatch_sig(const DevModel &m, F &&f)
         key |= (unsigned)m.roles[a] << (4 * a);
         if (m.roles[a] & ROLE_LJ) ty |= (unsigned)m.lj_type[a] << (4 * a);
     }
-    if (m.single_lj_at_com && ty == 0) return f.template operator()<SigStatic<1, ROLE_LJ, true>>();
-    // the two-centre models are compiled for the linear geometry only
-    if (m.linear && m.S == 2 && key == SIG_2CLJ && ty == 0)
-        return f.template operator()<SigStatic<2, SIG_2CLJ, false, 0, true>>();
-    // (their multipole site compiled at the centre of mass)
+    if (m.single_lj_at_com && ty == 0) return f.template operator()<Sig1CLJ>();
+    if (m.linear && m.S == 2 && key == SIG_2CLJ && ty == 0) return f.template operator()<Sig2CLJ>();
     if (m.linear && m.S == 3 && key == SIG_2CLJQ && ty == 0 && m.body[2][2] == 0.f)
-        return f.template operator()<SigStatic<3, SIG_2CLJQ, false, 0, true, 4u>>();
+        return f.template operator()<Sig2CLJQ>();
     if (m.linear && m.S == 3 && key == SIG_2CLJDQ && ty == 0 && m.body[2][2] == 0.f)
-        return f.template operator()<SigStatic<3, SIG_2CLJDQ, false, 0, true, 4u>>();
-    if (m.S == 5 && key == SIG_4SITE && ty == TY_4SITE)
-        return f.template operator()<SigStatic<5, SIG_4SITE, false, TY_4SITE>>();
+        return f.template operator()<Sig2CLJDQ>();
+    if (m.S == 5 && key == SIG_4SITE && ty == TY_4SITE) return f.template operator()<Sig4Site>();
     return f.template operator()<SigDyn>();
 }
 
@@ -365,7 +369,10 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
     } else {
         float4 uj = make_float4(0.f, 0.f, 0.f, 0.f);
         if constexpr (SIG::LIN) uj = __ldg(gj);  // the j molecule's axis
-#pragma unroll
+        // the run-time signature keeps its j-site loop rolled (its i-site
+        // loop stays unrolled, so the site totals stay in registers): a fully
+        // unrolled 8 x 8 site loop with run-time roles takes minutes to compile
+#pragma unroll(SIG::DYN ? 1 : S)
         for (int b = 0; b < S; b++) {
             const int rb = SIG::role(b, m);
             if (rb == 0) continue;
