@@ -12,13 +12,14 @@
 //     re-test in a narrow band, hits of consecutive i molecules packed into
 //     32-pair chunks;
 //   * FP32 site-site math (rsqrt/rcp on the MUFU pipe);
-//   * i side: a segmented warp sum per chunk into per-pass totals in shared
-//     memory;
-//   * Newton-3 side (half shell): reactions into per-candidate shared
-//     accumulators, one i of a chunk at a time; each staged window is
-//     flushed with 16-byte vector reductions into FP32 accumulator records,
-//     read directly by the integrator and converted to FP64 only on demand;
-//   * full shell: each ordered pair from both sides, plain FP64 stores of
+//   * half shell (Newton-3): each pair's terms go straight to the FP32
+//     accumulator records of i and j, two 16-byte vector reductions (F,
+//     tau) per molecule -- faster than per-candidate shared accumulators
+//     for j (a loop over the i's of a chunk, 6 KB of shared memory per warp)
+//     and than a segmented warp sum for i; the records are read directly by
+//     the integrator and converted to FP64 only on demand;
+//   * full shell: each ordered pair from both sides, a segmented warp sum
+//     per chunk into per-pass i totals in shared memory, plain FP64 stores of
 //     the per-molecule totals, bitwise deterministic;
 //   * no FP64 arithmetic per pair: GB300's FP64 rate is ~1/64 of FP32.
 #pragma once

@@ -31,25 +31,23 @@ struct ForceArgs {
 template <class SIG, int M>
 cudaError_t launch_force_sig(const ForceArgs &A, int half_shell, int n_blocks, cudaStream_t s);
 
-template <bool HALF>
 struct ForceExtra {
-    float4 jf[HALF ? JCAP : 1];  // Newton-3 reactions: F, tau_x
-    float2 jt[HALF ? JCAP : 1];  // tau_y, tau_z
-    float4 if4[32];              // i totals of the pass: F, tau_x
-    float2 it2[32];              // tau_y, tau_z
+    float4 if4[32];  // i totals of the pass: F, tau_x
+    float2 it2[32];  // tau_y, tau_z
 };
 
 template <class SIG, bool HALF>
 struct ForceOp {
     static constexpr int IMAX = 32;
     static constexpr int NQ = SIG::SINGLE ? 3 : 6;  // accumulated values per molecule: F, and tau unless single-site
-    using Tile = WarpTile<ForceExtra<HALF>>;
+    using Tile = WarpTile<ForceExtra>;
     const DevModel &m;
     const ForceArgs &A;
     int K;
     int ig;
     float pF0, pF1, pF2, pT0, pT1, pT2;            // the lane's pair of the current chunk (i side)
     float tq0, tq1, tq2;                           // its torque on j (half shell)
+    int pjs, psi;                                  // storage slots of its j and i
     float cU, cW, cX, cY, cZ;                      // pass sums of energy and virial (FP32)
     float sU, kU, sW, kW, sX, kX, sY, kY, sZ, kZ;  // compensated lane totals
     int nmol, nexam;
@@ -63,20 +61,15 @@ struct ForceOp {
     __device__ void pass_begin(int ig_, int ni, int lane)
     {
         ig = ig_;
-        for (int t = lane; t < ni; t += 32) {
-            T->x.if4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-            T->x.it2[t] = make_float2(0.f, 0.f);
+        if (!HALF) {  // the half shell adds its i terms per pair (chunk_end)
+            for (int t = lane; t < ni; t += 32) {
+                T->x.if4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                T->x.it2[t] = make_float2(0.f, 0.f);
+            }
         }
         cU = cW = cX = cY = cZ = 0.f;
     }
-    __device__ void seg_begin(Tile &TT, int nj, int lane)
-    {
-        if (HALF)
-            for (int t = lane; t < nj; t += 32) {
-                TT.x.jf[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (NQ == 6) TT.x.jt[t] = make_float2(0.f, 0.f);
-            }
-    }
+    __device__ void seg_begin(Tile &, int, int) {}
     __device__ void count_examined(int n) { nexam += n; }
     __device__ void pair(Tile &, const IMol<SIG> &I, int, float X0, float X1, float X2, int js)
     {
@@ -94,45 +87,38 @@ struct ForceOp {
         cY += X1 * Fp[1];
         cZ += X2 * Fp[2];
         nmol++;
+        pjs = js;
+        psi = I.slot;
         if (HALF) {
             tq0 = tq[0];
             tq1 = tq[1];
             tq2 = tq[2];
         }
     }
-    // End of a chunk.  j side (half shell): the Newton-3 reactions go into the
-    // staged candidates' shared accumulators one i at a time, since a j can
-    // meet two i's of a chunk but only once per i.  i side: a segmented suffix
-    // sum over the lanes; the first lane of each i adds the i's total.
-    __device__ void chunk_end(Tile &TT, int il, int k, bool valid, int lane)
+    // End of a chunk.  Half shell: each lane adds its pair's terms straight
+    // to the FP32 accumulator records of i and j (one 16-byte vector
+    // reduction for F and one for tau per molecule; measured faster than
+    // per-candidate shared accumulators for the Newton-3 side and than a
+    // segmented warp sum for the i side).  Full shell (deterministic): a
+    // segmented suffix sum over the lanes, the first lane of each i adding the
+    // i's total to the pass totals in shared memory.
+    __device__ void chunk_end(Tile &, int il, int, bool valid, int lane)
     {
+        if (HALF) {
+            if (valid) {
+                float *a = A.acc + (long long)FACC_STRIDE * psi;
+                red_add_v4(a, pF0, pF1, pF2, 0.f);
+                if (NQ == 6) red_add_v4(a + 4, pT0, pT1, pT2, 0.f);
+                float *b = A.acc + (long long)FACC_STRIDE * pjs;
+                red_add_v4(b, -pF0, -pF1, -pF2, 0.f);
+                if (NQ == 6) red_add_v4(b + 4, tq0, tq1, tq2, 0.f);
+            }
+            return;
+        }
         const int nvalid = __popc(__ballot_sync(FULLMASK, valid));  // valid lanes are a prefix
         const int prev = __shfl_up_sync(FULLMASK, il, 1);
         const bool head = valid && (lane == 0 || prev != il);
         const unsigned hm0 = __ballot_sync(FULLMASK, head);
-        if (HALF) {
-            unsigned hm = hm0;
-            while (hm) {  // warp-uniform: one i of the chunk at a time
-                const int h = __ffs(hm) - 1;
-                hm &= hm - 1;
-                const int e = hm ? __ffs(hm) - 1 : nvalid;
-                if (lane >= h && lane < e) {
-                    float4 a = TT.x.jf[k];
-                    a.x -= pF0;
-                    a.y -= pF1;
-                    a.z -= pF2;
-                    if (NQ == 6) {
-                        a.w += tq0;
-                        float2 b = TT.x.jt[k];
-                        b.x += tq1;
-                        b.y += tq2;
-                        TT.x.jt[k] = b;
-                    }
-                    TT.x.jf[k] = a;
-                }
-                __syncwarp();
-            }
-        }
         // lanes after this one in the same i segment
         const unsigned later = hm0 & ~((2u << lane) - 1u);
         const int rem = (later ? __ffs(later) - 1 : nvalid) - lane - 1;
@@ -161,43 +147,32 @@ struct ForceOp {
             T->x.if4[il] = a;
         }
     }
-    __device__ void seg_end(Tile &TT, int nj, int lane)
-    {
-        if (HALF)
-            for (int t = lane; t < nj; t += 32) {
-                const int js = __float_as_int(TT.jc[t].w);
-                float *a = A.acc + (long long)FACC_STRIDE * js;
-                const float4 f = TT.x.jf[t];
-                red_add_v4(a, f.x, f.y, f.z, 0.f);
-                if (NQ == 6) {
-                    const float2 b = TT.x.jt[t];
-                    red_add_v4(a + 4, f.w, b.x, b.y, 0.f);
-                }
-            }
-    }
+    __device__ void seg_end(Tile &, int, int) {}
     __device__ void pass_end(int s0, int ig_, int ni, int lane)
     {
-        for (int t = lane; t < ni; t += 32) {
-            const int si = s0 + ig_ + t;
-            const float4 i4 = T->x.if4[t];
-            const float2 i2 = T->x.it2[t];
-            const float ip[6] = {i4.x, i4.y, i4.z, i4.w, i2.x, i2.y};
-            if (HALF || A.to_acc) {
-                float *a = A.acc + (long long)FACC_STRIDE * si;
-                red_add_v4(a, ip[0], ip[1], ip[2], 0.f);
-                if (NQ == 6) red_add_v4(a + 4, ip[3], ip[4], ip[5], 0.f);
-            } else {
-                double *Fo = A.F + 3LL * si, *To = A.tau + 3LL * si;
-                const float t0 = NQ == 6 ? ip[3] : 0.f, t1 = NQ == 6 ? ip[4] : 0.f, t2 = NQ == 6 ? ip[5] : 0.f;
-                Fo[0] = ip[0];
-                Fo[1] = ip[1];
-                Fo[2] = ip[2];
-                To[0] = t0;
-                To[1] = t1;
-                To[2] = t2;
-                if (!(isfinite(ip[0]) && isfinite(ip[1]) && isfinite(ip[2]) && isfinite(t0) && isfinite(t1) &&
-                      isfinite(t2)))
-                    atomicExch(&A.flags[FLAG_NONFINITE], 1);
+        if (!HALF) {
+            for (int t = lane; t < ni; t += 32) {
+                const int si = s0 + ig_ + t;
+                const float4 i4 = T->x.if4[t];
+                const float2 i2 = T->x.it2[t];
+                const float ip[6] = {i4.x, i4.y, i4.z, i4.w, i2.x, i2.y};
+                if (A.to_acc) {
+                    float *a = A.acc + (long long)FACC_STRIDE * si;
+                    red_add_v4(a, ip[0], ip[1], ip[2], 0.f);
+                    if (NQ == 6) red_add_v4(a + 4, ip[3], ip[4], ip[5], 0.f);
+                } else {
+                    double *Fo = A.F + 3LL * si, *To = A.tau + 3LL * si;
+                    const float t0 = NQ == 6 ? ip[3] : 0.f, t1 = NQ == 6 ? ip[4] : 0.f, t2 = NQ == 6 ? ip[5] : 0.f;
+                    Fo[0] = ip[0];
+                    Fo[1] = ip[1];
+                    Fo[2] = ip[2];
+                    To[0] = t0;
+                    To[1] = t1;
+                    To[2] = t2;
+                    if (!(isfinite(ip[0]) && isfinite(ip[1]) && isfinite(ip[2]) && isfinite(t0) && isfinite(t1) &&
+                          isfinite(t2)))
+                        atomicExch(&A.flags[FLAG_NONFINITE], 1);
+                }
             }
         }
         kahan_add(sU, kU, cU);
