@@ -34,12 +34,16 @@ namespace {
 
 using namespace mdk;
 
-// Resident blocks the register budget is sized for: 4 blocks of 4 warps (at
-// most 128 registers) for models of up to 3 merged sites, 3 blocks (168) for
-// the larger compiled signatures, whose site loops spill at 128 registers,
-// and 2 for the run-time signature.
+// Resident blocks the register budget is sized for: 5 blocks of 4 warps (at
+// most 102 registers) for models of up to 3 merged sites without a dipole,
+// 4 (128) for the 3-site models with one, whose dipole terms spill at 102,
+// 3 (168) for the larger compiled signatures, whose site loops spill at 128
+// registers, and 2 for the run-time signature.
 template <class SIG>
-constexpr int force_min_blocks() { return SIG::DYN ? 2 : (SIG::S <= 3 ? 4 : 3); }
+constexpr int force_min_blocks()
+{
+    return SIG::DYN ? 2 : (SIG::S > 3 ? 3 : (sig_has_role(SIG::ROLES, SIG::S, ROLE_DIP) ? 4 : 5));
+}
 
 // Dynamic shared memory of one block: the warps' tiles, then (M = 2) their
 // stencil tables.

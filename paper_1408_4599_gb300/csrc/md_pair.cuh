@@ -7,16 +7,20 @@
 //   * the stencil cells' slots, counts and image offsets are loaded once
 //     (one lane per cell) and their candidate molecules staged in shared
 //     memory in windows of JCAP, image offset applied (FP32, i-cell frame);
-//   * for each i molecule the lanes test NTEST x 32 candidates per round
-//     (FP32 centre-of-mass distance; a test within a narrow band of r_c^2 is
-//     redone in FP64 from the FP64 state, so the pair set is the FP64
-//     definition's);
+//   * for each i molecule the lanes test NTEST x 32 candidates per round,
+//     or NTEST/2 x 32 when the i's candidates fit (a warp-uniform choice per
+//     i: single-site fluids stage ~130 candidates per cell, ~half a full
+//     round) (FP32 centre-of-mass distance; a test within a narrow band of
+//     r_c^2 is redone in FP64 from the FP64 state, so the pair set is the
+//     FP64 definition's);
 //   * hits are ballot-compacted into a per-warp queue shared by the i
 //     molecules of a pass and handed to the pair operation 32 at a time, so
 //     the expensive site-site math runs on packed lanes (only ~16% of the
 //     examined pairs interact, §3); the lanes of one i in a chunk are
 //     contiguous and their j's distinct.
 #pragma once
+
+#include <type_traits>
 
 #include "md_internal.cuh"
 
@@ -39,6 +43,12 @@ __host__ __device__ constexpr int sig_na(unsigned R, int S)
     for (int b = 0; b < S; b++) k += (sig_role(R, b) & AX_ROLES) ? 1 : 0;
     return k;
 }
+__host__ __device__ constexpr bool sig_has_role(unsigned R, int S, int role)
+{
+    for (int a = 0; a < S; a++)
+        if (sig_role(R, a) & role) return true;
+    return false;
+}
 __host__ __device__ constexpr unsigned sigkey(int r0, int r1 = 0, int r2 = 0, int r3 = 0, int r4 = 0, int r5 = 0,
                                               int r6 = 0, int r7 = 0)
 {
@@ -60,6 +70,7 @@ constexpr unsigned SIG_4SITE = sigkey(ROLE_LJ, ROLE_LJ | ROLE_CHG, ROLE_LJ | ROL
 template <int S_, unsigned R_, bool SINGLE_ = false, unsigned TY_ = 0, bool LIN_ = false, unsigned COM_ = 0>
 struct SigStatic {
     static constexpr int S = S_;
+    static constexpr unsigned ROLES = R_;  // 4 role bits per site
     static constexpr bool DYN = false;
     static constexpr bool SINGLE = SINGLE_;
     static constexpr bool LIN = LIN_;
@@ -76,6 +87,7 @@ struct SigStatic {
 // Run-time signature for any other model (up to MD_MAX_SITES sites).
 struct SigDyn {
     static constexpr int S = MD_MAX_SITES;
+    static constexpr unsigned ROLES = 0;  // roles known at run time only
     static constexpr bool DYN = true;
     static constexpr bool SINGLE = false;
     static constexpr bool LIN = false;
@@ -753,12 +765,13 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
                     const double e2 = __dsub_rn(__dsub_rn(ri[2], rj[2]), (double)kz * g.L[2]);
                     return __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2)) < g.rc2;
                 };
-                // NTEST candidates per lane per round (independent tests),
+                // one test round: NT candidates per lane (independent tests),
                 // then the hits are appended in candidate order
-                for (int kb = skip_to; kb < nj; kb += 32 * NTEST) {
-                    bool h[NTEST], near[NTEST], any_near = false;
+                auto round = [&](auto ntc, int kb) {
+                    constexpr int NT = decltype(ntc)::value;
+                    bool h[NT], near[NT], any_near = false;
 #pragma unroll
-                    for (int u = 0; u < NTEST; u++) {
+                    for (int u = 0; u < NT; u++) {
                         const float d2 = dist2(kb + 32 * u + lane);
                         h[u] = d2 < g.rc2f;
                         near[u] = fabsf(d2 - g.rc2f) < g.bandf;
@@ -766,11 +779,11 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
                     }
                     if (__any_sync(FULLMASK, any_near)) {  // rare: decide in FP64
 #pragma unroll
-                        for (int u = 0; u < NTEST; u++)
+                        for (int u = 0; u < NT; u++)
                             if (near[u]) h[u] = test64(kb + 32 * u + lane);
                     }
 #pragma unroll
-                    for (int u = 0; u < NTEST; u++) {
+                    for (int u = 0; u < NT; u++) {
                         const unsigned bal = __ballot_sync(FULLMASK, h[u]);
                         if (h[u]) T.queue[qn + __popc(bal & lt_mask)] = tag | (kb + 32 * u + lane);
                         qn += __popc(bal);
@@ -783,6 +796,12 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
                         qn -= 32;
                         __syncwarp();
                     }
+                };
+                // warp-uniform: half-width rounds when the i's candidates fit
+                if (nj - skip_to <= 32 * (NTEST / 2)) {
+                    round(std::integral_constant<int, NTEST / 2>{}, skip_to);
+                } else {
+                    for (int kb = skip_to; kb < nj; kb += 32 * NTEST) round(std::integral_constant<int, NTEST>{}, kb);
                 }
                 if (lane == 0) op.count_examined(nj - skip_to - (self_k >= 0 ? 1 : 0));
             }
