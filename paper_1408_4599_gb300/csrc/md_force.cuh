@@ -35,14 +35,16 @@ namespace {
 using namespace mdk;
 
 // Resident blocks the register budget is sized for: 5 blocks of 4 warps (at
-// most 102 registers) for models of up to 3 merged sites without a dipole,
-// 4 (128) for the 3-site models with one, whose dipole terms spill at 102,
-// 3 (168) for the larger compiled signatures, whose site loops spill at 128
-// registers, and 2 for the run-time signature.
-template <class SIG>
+// most 102 registers) for the half shell of models of up to 3 merged sites
+// without a dipole; 4 (128) for their full shell (its segmented i sums and
+// FP64 stores ran 10% slower under the tighter cap) and for the 3-site
+// models with a dipole, whose dipole terms spill at 102; 3 (168) for the
+// larger compiled signatures, whose site loops spill at 128 registers; 2 for
+// the run-time signature.
+template <class SIG, bool HALF>
 constexpr int force_min_blocks()
 {
-    return SIG::DYN ? 2 : (SIG::S > 3 ? 3 : (sig_has_role(SIG::ROLES, SIG::S, ROLE_DIP) ? 4 : 5));
+    return SIG::DYN ? 2 : (SIG::S > 3 ? 3 : ((!HALF || sig_has_role(SIG::ROLES, SIG::S, ROLE_DIP)) ? 4 : 5));
 }
 
 // Dynamic shared memory of one block: the warps' tiles, then (M = 2) their
@@ -55,7 +57,7 @@ constexpr size_t force_smem()
 
 // M: stencil radius in cells (1: cells of edge >= r_c; 2: >= r_c / 2).
 template <class SIG, bool HALF, int M>
-__global__ void __launch_bounds__(MD_WARPS * 32, force_min_blocks<SIG>()) k_force(const __grid_constant__ ForceArgs A)
+__global__ void __launch_bounds__(MD_WARPS * 32, force_min_blocks<SIG, HALF>()) k_force(const __grid_constant__ ForceArgs A)
 {
     using Op = ForceOp<SIG, HALF>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
