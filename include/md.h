@@ -286,9 +286,9 @@ const char *md_batch_last_error(const md_batch *b);
  * them (v(t) = v + dt/2 F/m, j(t) = j + dt/2 tau, w = I^-1 R(q)^T j(t)),
  * but as a stand-alone call that allocates no memory.  The paper has no
  * counterpart; this entry point exists for callers that cannot allocate:
- * code running inside CUDA stream capture (allocation cannot be captured),
- * programs whose own allocator owns the device memory, and loops that must
- * not incur the synchronisation of cudaFree.
+ * programs whose own allocator has reserved the device memory up front and
+ * must account for every byte, and loops that must not incur the
+ * device-wide synchronisation of cudaFree.
  *   n: molecules, at most 8,388,608 (MD_ERR_OVERFLOW beyond).
  *   v, j, F, tau: device, n x 3 FP64; q: device, n x 4 FP64 unit
  *   quaternions; mass > 0 and the principal moments I[3] (host, >= 0; a

@@ -1,16 +1,16 @@
 // md_noalloc.cu -- md_kinetic_noalloc: the kinetic-energy reduction of
 // md_energy_virial as a stand-alone entry point that allocates no memory.
 //
-// Some callers cannot call cudaMalloc (or anything that does): code that
-// runs while a stream is being captured into a CUDA graph (allocation is
-// not a capturable operation and, in the global capture mode, is an error
-// during capture), applications whose own allocator has reserved the
-// device memory up front and must account for every byte, and real-time
-// loops that must not stall on the device-wide synchronisation that
-// cudaFree implies.  For them this entry point keeps its scratch -- the
-// per-block partial sums of the reduction -- in a file-scope device array
-// of fixed size, which every GPU that loads the library holds until the
-// process exits.
+// Some callers cannot call cudaMalloc (or anything that does):
+// applications whose own allocator has reserved the device memory up front
+// and must account for every byte, and real-time loops that must not stall
+// on the device-wide synchronisation that cudaFree implies.  For them this
+// entry point keeps its scratch -- the per-block partial sums of the
+// reduction -- in a file-scope device array of fixed size, which every GPU
+// that loads the library holds until the process exits.  The first call on
+// a device looks up the array's device address (so that first call should
+// come before any stream capture); calls that overlap on the GPU race on
+// the shared array.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -113,7 +113,8 @@ extern "C" md_status md_kinetic_noalloc(int64_t n, const double *v, const double
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return MD_ERR_CUDA;
     double *scratch = nullptr;
     {
-        // one-time set-up per device, with that device current
+        // one-time set-up per device, done by the first call on that device
+        // with the device current
         std::lock_guard<std::mutex> lk(g_mu);
         if (!g_scratch_ptr[dev]) {
             void *p = nullptr;
