@@ -54,7 +54,7 @@ typedef enum {
     MD_ERR_NONFINITE = -6,   /* non-finite force, torque or position detected */
     MD_ERR_OVERFLOW = -7,    /* a fixed-capacity buffer would overflow */
     MD_ERR_TIMEOUT = -8,     /* a bounded device wait gave up */
-    MD_ERR_UNSUPPORTED = -9  /* valid input outside what this build supports */
+    MD_ERR_UNSUPPORTED = -9  /* valid input outside what the library supports */
 } md_status;
 
 /* One rigid component (molecule type), §2 "rigid rotators".  Positions are
@@ -90,7 +90,7 @@ typedef struct {
     const double *sigma;
     const double *xi;
     const double *eta;
-    int32_t n_comp;          /* this build: exactly 1 */
+    int32_t n_comp;          /* exactly 1 (one component per system) */
     const md_component *comp;
 } md_site_types;
 

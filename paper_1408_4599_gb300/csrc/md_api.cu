@@ -606,7 +606,7 @@ const char *md_status_str(md_status st)
     case MD_ERR_NONFINITE: return "MD_ERR_NONFINITE: non-finite value detected";
     case MD_ERR_OVERFLOW: return "MD_ERR_OVERFLOW: buffer capacity exceeded";
     case MD_ERR_TIMEOUT: return "MD_ERR_TIMEOUT: bounded device wait gave up";
-    case MD_ERR_UNSUPPORTED: return "MD_ERR_UNSUPPORTED: input outside this build's support";
+    case MD_ERR_UNSUPPORTED: return "MD_ERR_UNSUPPORTED: input outside what the library supports";
     }
     return "unknown md_status";
 }
