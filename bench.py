@@ -65,7 +65,9 @@ def force_traffic():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms; start()
+    returns once the first sample has arrived (at most 3 s), so that the
+    timed region that follows is sampled."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -76,15 +78,19 @@ class ClockSampler:
         self.rows = []
         self.proc = None
 
-    def start(self):
+    def start(self, wait_s=3.0):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while not self.rows and self.proc.poll() is None and time.perf_counter() - t0 < wait_s:
+            time.sleep(0.005)
 
     def _read(self):
         for line in self.proc.stdout:
