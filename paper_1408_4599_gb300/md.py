@@ -158,12 +158,20 @@ def _stream_ptr(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
-def _ptr(a):
-    """(pointer, on_device, keepalive) of a numpy array or torch tensor (FP64, contiguous)."""
+def _ptr(a, out=False):
+    """(pointer, on_device, keepalive) of a numpy array or torch tensor (FP64,
+    contiguous).  A host input of another dtype or layout is passed as a
+    converted copy; an output (out=True) must already be a writable
+    C-contiguous float64 array, since the library writes through the pointer
+    and a copy would silently drop the result."""
     if a is None:
         return None, 0, None
     if isinstance(a, np.ndarray):
-        a = np.ascontiguousarray(a, dtype=np.float64)
+        if out:
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or not a.flags["WRITEABLE"]:
+                raise ValueError("output arrays passed to the MD ABI must be writable C-contiguous float64")
+        else:
+            a = np.ascontiguousarray(a, dtype=np.float64)
         return C.c_void_p(a.ctypes.data), 0, a
     import torch
     if isinstance(a, torch.Tensor):
@@ -171,6 +179,14 @@ def _ptr(a):
             raise ValueError("tensors passed to the MD ABI must be contiguous float64")
         return C.c_void_p(a.data_ptr()), int(a.is_cuda), a
     raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _need_rows(n, w, **arrays):
+    """Every given array (numpy or torch) must have shape (n, w): the library
+    reads or writes exactly n rows of w doubles through each pointer."""
+    for name, a in arrays.items():
+        if a is not None and tuple(a.shape) != (n, w):
+            raise ValueError(f"{name} has shape {tuple(a.shape)}, expected ({n}, {w})")
 
 
 class Model:
@@ -248,6 +264,8 @@ def md_set_molecules(h, r, q, v=None, j=None, stream=None):
     if len(devs) != 1:
         raise ValueError("all arrays must live on the same side (host or device)")
     n = (k1.shape[0] if k1 is not None else 0)
+    _need_rows(n, 3, r=k1, v=k3, j=k4)
+    _need_rows(n, 4, q=k2)
     _check(lib().md_set_molecules(h, n, None, rp, vp, qp, jp, dev, _stream_ptr(stream)), h)
 
 
@@ -271,7 +289,10 @@ def md_get_molecules(h, r=None, v=None, q=None, j=None, stream=None):
     if r is None and v is None and q is None and j is None:
         n = lib().md_n_molecules(h)
         r, v, q, j = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 4)), np.zeros((n, 3))
-    ptrs = [_ptr(a) for a in (r, v, q, j)]
+    ptrs = [_ptr(a, out=True) for a in (r, v, q, j)]
+    n = lib().md_n_molecules(h)
+    _need_rows(n, 3, r=r, v=v, j=j)
+    _need_rows(n, 4, q=q)
     dev = max(p[1] for p in ptrs)
     _check(lib().md_get_molecules(h, *[p[0] for p in ptrs], dev, _stream_ptr(stream)), h)
     return r, v, q, j
@@ -281,7 +302,8 @@ def md_get_forces(h, F=None, tau=None, stream=None):
     if F is None and tau is None:
         n = lib().md_n_molecules(h)
         F, tau = np.zeros((n, 3)), np.zeros((n, 3))
-    pf, pt = _ptr(F), _ptr(tau)
+    pf, pt = _ptr(F, out=True), _ptr(tau, out=True)
+    _need_rows(lib().md_n_molecules(h), 3, F=F, tau=tau)
     dev = max(pf[1], pt[1])
     _check(lib().md_get_forces(h, pf[0], pt[0], dev, _stream_ptr(stream)), h)
     return F, tau
@@ -323,6 +345,8 @@ def md_param_grad(h, r_all, q_all, stream=None):
     qp, dq, qk = _ptr(q_all)
     if dev != dq:
         raise ValueError("r_all and q_all must live on the same side")
+    if len(rk.shape) != 3 or rk.shape[2] != 3 or tuple(qk.shape) != (rk.shape[0], rk.shape[1], 4):
+        raise ValueError(f"r_all {tuple(rk.shape)} and q_all {tuple(qk.shape)} must be n_cfg x n x 3 and x 4")
     n_cfg, n = int(rk.shape[0]), int(rk.shape[1])
     P = md_n_params(h)
     dU, dW, means = np.zeros(P), np.zeros(P), np.zeros(2)
@@ -333,11 +357,15 @@ def md_param_grad(h, r_all, q_all, stream=None):
 
 def md_kinetic_noalloc(v, q, j, F, tau, mass, moments, dt, K_out, stream=None):
     """K_out (device float64 tensor of 2) <- (K_trans, K_rot); allocates nothing."""
-    ptrs = [_ptr(a) for a in (v, q, j, F, tau, K_out)]
+    ptrs = [_ptr(a) for a in (v, q, j, F, tau)] + [_ptr(K_out, out=True)]
     if min(p[1] for p in ptrs) != 1:
         raise ValueError("md_kinetic_noalloc takes device tensors only")
     I = (C.c_double * 3)(*[float(x) for x in moments])
     n = ptrs[0][2].shape[0]
+    _need_rows(n, 3, v=v, j=j, F=F, tau=tau)
+    _need_rows(n, 4, q=q)
+    if K_out.numel() < 2:
+        raise ValueError("K_out must hold 2 doubles")
     _check(lib().md_kinetic_noalloc(n, *[p[0] for p in ptrs[:5]], float(mass), I, float(dt), ptrs[5][0],
                                     _stream_ptr(stream)))
 
@@ -426,6 +454,9 @@ class Batch:
             v = np.concatenate([c["v"] for c in self.cfgs])
             j = np.concatenate([c["j"] for c in self.cfgs])
         ptrs = [_ptr(a) for a in (r, v, q, j)]
+        nt = int(self.n_per.sum())
+        _need_rows(nt, 3, r=ptrs[0][2], v=ptrs[1][2], j=ptrs[3][2])
+        _need_rows(nt, 4, q=ptrs[2][2])
         dev = ptrs[0][1]
         n = self.n_per.ctypes.data_as(C.POINTER(C.c_int64))
         _bcheck(lib().md_batch_set_molecules(self.h, n, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], dev,

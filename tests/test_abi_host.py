@@ -108,3 +108,39 @@ def test_null_handle_calls_fail_cleanly():
     assert L.md_energy_virial(None, None) == -1
     assert L.md_n_molecules(None) == -1
     L.md_destroy(None)
+
+
+def test_binding_refuses_mismatched_state_shapes():
+    """The library reads n rows of every state array (n from r), so the
+    binding refuses arrays of other shapes before any library call."""
+    r = np.zeros((5, 3))
+    with pytest.raises(ValueError, match=r"q has shape \(4, 4\)"):
+        md.md_set_molecules(None, r, np.zeros((4, 4)))
+    with pytest.raises(ValueError, match=r"v has shape \(5, 4\)"):
+        md.md_set_molecules(None, r, np.zeros((5, 4)), v=np.zeros((5, 4)))
+    with pytest.raises(ValueError, match=r"r has shape \(15,\)"):
+        md.md_set_molecules(None, r.ravel(), np.zeros((5, 4)))
+
+
+def test_binding_refuses_outputs_it_would_have_to_copy():
+    """Host output arrays are written through their pointer: a float32,
+    strided or read-only array would receive nothing, so it is refused."""
+    for bad in (np.zeros((4, 3), dtype=np.float32), np.zeros((4, 6))[:, ::2]):
+        with pytest.raises(ValueError, match="writable C-contiguous float64"):
+            md.md_get_forces(None, F=bad)
+        with pytest.raises(ValueError, match="writable C-contiguous float64"):
+            md.md_get_molecules(None, r=bad)
+    ro = np.zeros((4, 3))
+    ro.flags.writeable = False
+    with pytest.raises(ValueError, match="writable C-contiguous float64"):
+        md.md_get_molecules(None, v=ro)
+    # inputs of another dtype or layout are converted, not refused
+    p, on_dev, keep = md._ptr(np.zeros((4, 6), dtype=np.float32)[:, ::2])
+    assert on_dev == 0 and keep.dtype == np.float64 and keep.flags["C_CONTIGUOUS"]
+
+
+def test_binding_refuses_misshaped_ensembles():
+    with pytest.raises(ValueError, match="n_cfg x n x 3"):
+        md.md_param_grad(None, np.zeros((2, 5, 3)), np.zeros((2, 4, 4)))
+    with pytest.raises(ValueError, match="n_cfg x n x 3"):
+        md.md_param_grad(None, np.zeros((5, 3)), np.zeros((5, 4)))
