@@ -73,14 +73,26 @@ class ClockSampler:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
-        self.idx = gpu_index
+    def __init__(self, device):
+        """device: the torch device whose GPU is sampled.  nvidia-smi is
+        addressed by the GPU's UUID: torch's device index is logical (under
+        CUDA_VISIBLE_DEVICES), nvidia-smi's --id index is physical."""
+        import torch
+        self.uuid = None
+        try:
+            u = str(torch.cuda.get_device_properties(device).uuid)
+            self.uuid = u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            pass
         self.rows = []
         self.proc = None
+        self.t = None
 
     def start(self, wait_s=3.0):
+        if self.uuid is None:
+            return
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.uuid}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
@@ -105,7 +117,9 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-        res = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.rows)}
+        if self.t is not None:
+            self.t.join(timeout=5)  # the reader has seen the end of the pipe
+        res = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.rows), "gpu_uuid": self.uuid}
         if not self.rows:
             return res
         sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
@@ -255,7 +269,7 @@ def main():
 
     md.md_profile(sysm.h, True)
     md.md_kernel_times_get(sysm.h)  # reset
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(dev)
     clocks.start()
     if world > 1:
         torch.distributed.barrier()
@@ -387,7 +401,7 @@ def run_single(args, md, torch, dev, rank):
     # L2 flushed before every timed step unless the state alone exceeds the
     # 129 MB L2 (the 200M point: ~70 GB on the device, no room for a buffer)
     flush = None if evals_only else torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    clocks = ClockSampler(dev.index or 0)
+    clocks = ClockSampler(dev)
     clocks.start()
     torch.cuda.synchronize()
     t = timed_calls(lambda: s.compute_forces() if evals_only else s.step(1, cfg["dt"]), steps, stream, torch, flush)
@@ -515,7 +529,7 @@ def run_batch(args, md, torch, dev, rank):
     tune = b.tune()
     b.step(args.warmup, dt, use_graph=True)
     o0 = b.observables()
-    clocks = ClockSampler(dev.index or 0)
+    clocks = ClockSampler(dev)
     clocks.start()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -299,10 +299,27 @@ const char *md_batch_last_error(const md_batch *b);
  * looks up the array's device address with that device current, so make
  * that first call before any stream capture.  All calls share the scratch:
  * calls whose work overlaps on the GPU (e.g. on different streams) race.
+ * The looked-up address is kept for the life of the process, so a device
+ * reset (cudaDeviceReset) after the first call on that device is not
+ * supported.  MD_ERR_CUDA reports a failed look-up or launch of this call
+ * only; an earlier error left pending by other work is not consumed.
  * Errors: MD_ERR_ARG, MD_ERR_OVERFLOW, MD_ERR_CUDA. */
 md_status md_kinetic_noalloc(int64_t n, const double *v, const double *q, const double *j, const double *F,
                              const double *tau, double mass, const double I[3], double dt, double *K_out,
                              void *cuda_stream);
+
+/* Measured FP32 FMA throughput of the current GPU: a full-occupancy grid of
+ * threads, each running eight independent FMA chains, timed with CUDA
+ * events on cuda_stream (best of three launches after one warm-up, ~5 ms
+ * each).  paired = 0 issues scalar fma.rn.f32; paired = 1 the paired
+ * fma.rn.f32x2 (two FMAs per instruction on sm_100-class GPUs).
+ * out[0] = FLOP/s (an FMA counts 2), out[1] = ms of the best launch (host,
+ * 2 doubles).  The paper has no counterpart: this is the measured
+ * denominator of the force kernel's FP32 roofline, beside the unit-count
+ * figure SMs x 128 lanes x 2 x clock.  Allocates and frees a small sink
+ * buffer; synchronising.  Errors: MD_ERR_ARG (NULL out, paired not 0/1),
+ * MD_ERR_OOM, MD_ERR_CUDA. */
+md_status md_fp32_peak(int32_t paired, double *out, void *cuda_stream);
 
 void md_destroy(md_system *sys);
 const char *md_status_str(md_status s);

@@ -10,7 +10,9 @@
 // that loads the library holds until the process exits.  The first call on
 // a device looks up the array's device address (so that first call should
 // come before any stream capture); calls that overlap on the GPU race on
-// the shared array.
+// the shared array.  The address is kept per device ordinal for the life of
+// the process: resetting a device (cudaDeviceReset) after the first call on
+// it is not supported.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -139,10 +141,18 @@ extern "C" md_status md_kinetic_noalloc(int64_t n, const double *v, const double
     a.dt_half = 0.5 * dt;
     a.scratch = scratch;
     int nb = (int)((n + NA_CHUNK - 1) / NA_CHUNK);
+    // each launch's own status (cudaLaunchKernel returns it), so that an
+    // earlier, unrelated error left in the runtime's last-error slot is
+    // neither reported here nor cleared
     if (nb > 0) {
-        k_kin_partial<<<nb, NA_THREADS, 0, st>>>(a);
+        void *args1[] = {&a};
+        if (cudaLaunchKernel((const void *)k_kin_partial, dim3(nb), dim3(NA_THREADS), args1, 0, st) != cudaSuccess)
+            return MD_ERR_CUDA;
     }
     // every block partial that phase 2 reads was written by this call's phase 1
-    k_kin_final<<<1, 32, 0, st>>>(scratch, nb, K_out);
-    return cudaGetLastError() == cudaSuccess ? MD_OK : MD_ERR_CUDA;
+    const double *sc = scratch;
+    void *args2[] = {&sc, &nb, &K_out};
+    if (cudaLaunchKernel((const void *)k_kin_final, dim3(1), dim3(32), args2, 0, st) != cudaSuccess)
+        return MD_ERR_CUDA;
+    return MD_OK;
 }

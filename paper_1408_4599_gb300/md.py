@@ -69,7 +69,8 @@ EXPORTS = ("md_create", "md_set_molecules", "md_compute_forces", "md_step", "md_
            "md_destroy", "md_status_str", "md_last_error", "md_n_params", "md_get_params", "md_set_params",
            "md_param_grad", "md_batch_create", "md_batch_set_molecules", "md_batch_compute_forces", "md_batch_step",
            "md_batch_energy_virial", "md_batch_get_molecules", "md_batch_get_forces", "md_batch_tune",
-           "md_batch_destroy", "md_batch_last_error", "md_batch_set_thermostat", "md_kinetic_noalloc")
+           "md_batch_destroy", "md_batch_last_error", "md_batch_set_thermostat", "md_kinetic_noalloc",
+           "md_fp32_peak")
 
 
 def lib():
@@ -118,6 +119,8 @@ def lib():
             getattr(L, name).restype = C.c_int
         L.md_kinetic_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, C.c_double, dp, C.c_double, vp, vp]
         L.md_kinetic_noalloc.restype = C.c_int
+        L.md_fp32_peak.argtypes = [i32, dp, vp]
+        L.md_fp32_peak.restype = C.c_int
         L.md_destroy.argtypes = [vp]
         L.md_destroy.restype = None
         L.md_status_str.argtypes = [C.c_int]
@@ -179,6 +182,27 @@ def _ptr(a, out=False):
             raise ValueError("tensors passed to the MD ABI must be contiguous float64")
         return C.c_void_p(a.data_ptr()), int(a.is_cuda), a
     raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _side(entries):
+    """The on_device flag shared by every given (pointer, on_device, keep)
+    entry of _ptr.  The library takes one flag per call for all of its
+    pointers, so host arrays mixed with CUDA tensors are refused (a host
+    pointer would be handed to a kernel as a device address), and so are
+    CUDA tensors on a device other than the current one (the library
+    launches on the current device)."""
+    live = [e for e in entries if e[0] is not None]
+    sides = {e[1] for e in live}
+    if len(sides) > 1:
+        raise ValueError("all arrays of one call must live on the same side (host or device)")
+    dev = sides.pop() if sides else 0
+    if dev:
+        import torch
+        cur = torch.cuda.current_device()
+        for e in live:
+            if e[2].device.index != cur:
+                raise ValueError(f"CUDA tensor on {e[2].device}, but the current device is cuda:{cur}")
+    return dev
 
 
 def _need_rows(n, w, **arrays):
@@ -260,9 +284,7 @@ def md_set_molecules(h, r, q, v=None, j=None, stream=None):
     qp, dq, k2 = _ptr(q)
     vp, dv, k3 = _ptr(v)
     jp, dj, k4 = _ptr(j)
-    devs = {x for x, p in ((dev, rp), (dq, qp), (dv, vp), (dj, jp)) if p is not None}
-    if len(devs) != 1:
-        raise ValueError("all arrays must live on the same side (host or device)")
+    dev = _side([(rp, dev, k1), (qp, dq, k2), (vp, dv, k3), (jp, dj, k4)])
     n = (k1.shape[0] if k1 is not None else 0)
     _need_rows(n, 3, r=k1, v=k3, j=k4)
     _need_rows(n, 4, q=k2)
@@ -290,10 +312,10 @@ def md_get_molecules(h, r=None, v=None, q=None, j=None, stream=None):
         n = lib().md_n_molecules(h)
         r, v, q, j = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 4)), np.zeros((n, 3))
     ptrs = [_ptr(a, out=True) for a in (r, v, q, j)]
+    dev = _side(ptrs)
     n = lib().md_n_molecules(h)
     _need_rows(n, 3, r=r, v=v, j=j)
     _need_rows(n, 4, q=q)
-    dev = max(p[1] for p in ptrs)
     _check(lib().md_get_molecules(h, *[p[0] for p in ptrs], dev, _stream_ptr(stream)), h)
     return r, v, q, j
 
@@ -303,8 +325,8 @@ def md_get_forces(h, F=None, tau=None, stream=None):
         n = lib().md_n_molecules(h)
         F, tau = np.zeros((n, 3)), np.zeros((n, 3))
     pf, pt = _ptr(F, out=True), _ptr(tau, out=True)
+    dev = _side([pf, pt])
     _need_rows(lib().md_n_molecules(h), 3, F=F, tau=tau)
-    dev = max(pf[1], pt[1])
     _check(lib().md_get_forces(h, pf[0], pt[0], dev, _stream_ptr(stream)), h)
     return F, tau
 
@@ -343,8 +365,7 @@ def md_param_grad(h, r_all, q_all, stream=None):
     (n_cfg x n x 3) and q_all (n_cfg x n x 4), host arrays or device tensors."""
     rp, dev, rk = _ptr(r_all)
     qp, dq, qk = _ptr(q_all)
-    if dev != dq:
-        raise ValueError("r_all and q_all must live on the same side")
+    dev = _side([(rp, dev, rk), (qp, dq, qk)])
     if len(rk.shape) != 3 or rk.shape[2] != 3 or tuple(qk.shape) != (rk.shape[0], rk.shape[1], 4):
         raise ValueError(f"r_all {tuple(rk.shape)} and q_all {tuple(qk.shape)} must be n_cfg x n x 3 and x 4")
     n_cfg, n = int(rk.shape[0]), int(rk.shape[1])
@@ -360,6 +381,7 @@ def md_kinetic_noalloc(v, q, j, F, tau, mass, moments, dt, K_out, stream=None):
     ptrs = [_ptr(a) for a in (v, q, j, F, tau)] + [_ptr(K_out, out=True)]
     if min(p[1] for p in ptrs) != 1:
         raise ValueError("md_kinetic_noalloc takes device tensors only")
+    _side(ptrs)  # one device, the current one (the file-scope scratch is per device)
     I = (C.c_double * 3)(*[float(x) for x in moments])
     n = ptrs[0][2].shape[0]
     _need_rows(n, 3, v=v, j=j, F=F, tau=tau)
@@ -368,6 +390,14 @@ def md_kinetic_noalloc(v, q, j, F, tau, mass, moments, dt, K_out, stream=None):
         raise ValueError("K_out must hold 2 doubles")
     _check(lib().md_kinetic_noalloc(n, *[p[0] for p in ptrs[:5]], float(mass), I, float(dt), ptrs[5][0],
                                     _stream_ptr(stream)))
+
+
+def md_fp32_peak(paired=False, stream=None):
+    """(FLOP/s, ms) of the FMA-chain peak kernel: scalar FMA, or with paired
+    the two-wide fma.rn.f32x2."""
+    out = np.zeros(2)
+    _check(lib().md_fp32_peak(int(bool(paired)), out.ctypes.data_as(dp), _stream_ptr(stream)))
+    return float(out[0]), float(out[1])
 
 
 def md_destroy(h):
@@ -457,7 +487,7 @@ class Batch:
         nt = int(self.n_per.sum())
         _need_rows(nt, 3, r=ptrs[0][2], v=ptrs[1][2], j=ptrs[3][2])
         _need_rows(nt, 4, q=ptrs[2][2])
-        dev = ptrs[0][1]
+        dev = _side(ptrs)
         n = self.n_per.ctypes.data_as(C.POINTER(C.c_int64))
         _bcheck(lib().md_batch_set_molecules(self.h, n, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], dev,
                                              _stream_ptr(stream)), self.h)

@@ -144,3 +144,51 @@ def test_binding_refuses_misshaped_ensembles():
         md.md_param_grad(None, np.zeros((2, 5, 3)), np.zeros((2, 4, 4)))
     with pytest.raises(ValueError, match="n_cfg x n x 3"):
         md.md_param_grad(None, np.zeros((5, 3)), np.zeros((5, 4)))
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA tensor on a CPU-only machine: the binding sees
+    on_device = 1 for it (through a patched _ptr) and never dereferences it."""
+
+    def __init__(self, shape, index=0):
+        self.shape = shape
+        self.device = type("Dev", (), {"index": index, "__str__": lambda s: f"cuda:{index}"})()
+
+
+def _patch_fake_cuda(monkeypatch):
+    real = md._ptr
+
+    def fake_ptr(a, out=False):
+        if isinstance(a, _FakeCudaTensor):
+            return C.c_void_p(0x1000), 1, a
+        return real(a, out)
+
+    monkeypatch.setattr(md, "_ptr", fake_ptr)
+    monkeypatch.setattr(md, "lib", lambda: pytest.fail("the library was called"))
+
+
+def test_binding_refuses_host_outputs_mixed_with_device_outputs(monkeypatch):
+    """md_get_molecules / md_get_forces take one on_device flag for all
+    pointers: a host array beside a CUDA tensor would reach a kernel as a
+    device address, so the mix is refused before any library call."""
+    _patch_fake_cuda(monkeypatch)
+    with pytest.raises(ValueError, match="same side"):
+        md.md_get_molecules(None, r=np.zeros((4, 3)), v=_FakeCudaTensor((4, 3)))
+    with pytest.raises(ValueError, match="same side"):
+        md.md_get_forces(None, F=np.zeros((4, 3)), tau=_FakeCudaTensor((4, 3)))
+    with pytest.raises(ValueError, match="same side"):
+        md.md_set_molecules(None, np.zeros((4, 3)), _FakeCudaTensor((4, 4)))
+
+
+def test_binding_refuses_tensors_off_the_current_device(monkeypatch):
+    """The library launches on the current device, so a CUDA tensor on any
+    other device is refused (md_kinetic_noalloc's scratch is per device)."""
+    torch = pytest.importorskip("torch")
+    _patch_fake_cuda(monkeypatch)
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    with pytest.raises(ValueError, match="current device is cuda:0"):
+        md.md_get_forces(None, F=_FakeCudaTensor((4, 3), 0), tau=_FakeCudaTensor((4, 3), 1))
+    t3 = [_FakeCudaTensor((4, 3), 0) for _ in range(4)]
+    with pytest.raises(ValueError, match="current device is cuda:0"):
+        md.md_kinetic_noalloc(t3[0], _FakeCudaTensor((4, 4), 1), t3[1], t3[2], t3[3], 1.0, (1.0, 1.0, 0.0), 0.001,
+                              _FakeCudaTensor((2,), 0))

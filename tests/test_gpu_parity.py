@@ -81,6 +81,10 @@ def check_parity(name, cfg, F, tau, obs, Fo, to, oo, exact_examined=True):
         assert abs(obs["W_" + k[1:]] - oo[k]) <= 1e-5 * oo["abs_W"]
     assert obs["U_lrc"] == pytest.approx(oo["U_lrc"], rel=1e-12, abs=1e-300)
     assert obs["W_lrc"] == pytest.approx(oo["W_lrc"], rel=1e-12, abs=1e-300)
+    # reaction-field self energy (reading R4), reported apart from U_pot
+    assert obs["U_rf_self"] == pytest.approx(oo["U_rf_self"], rel=1e-12, abs=1e-300)
+    if any(d["mu"] != 0 for d in cfg["model"]["dipoles"]) and cfg.get("eps_rf", math.inf) != 1.0:
+        assert obs["U_rf_self"] < 0.0
 
 
 CASES = {

@@ -245,6 +245,63 @@ def test_reaction_field_conducting_limit_is_method_of_images():
     assert (oi["U"] - ov["U"]) * mu_i * mu_j == pytest.approx(U_img, rel=1e-7)
 
 
+def test_reaction_field_self_energy_is_method_of_images():
+    """§3 reaction field, self term (reading R4): a molecule's own dipoles at
+    the centre of a grounded conducting cavity of radius rc (eps_RF = inf)
+    meet the field of their own images.  Two dipoles of one molecule as
+    explicit +-q pairs at the centre, Kelvin images of every charge, half
+    the charge-image energy, h -> 0: -|sum_a mu_a e_a|^2 / (2 rc^3) per
+    molecule.  Pins the sign, the 1/2, the rc^-3 and the cross term of two
+    dipoles of one molecule."""
+    rc = 3.0
+    dips = [(1.1, np.array([0.6, 0.0, 0.8])), (0.7, np.array([0.0, 1.0, 0.0]))]
+
+    def images_self_energy(h):
+        ch = []
+        for mu, e in dips:
+            ch += [(mu / h, 0.5 * h * e), (-mu / h, -0.5 * h * e)]
+        U = 0.0
+        for qk, sk in ch:
+            ns = np.linalg.norm(sk)
+            qim, sim = -qk * rc / ns, sk * rc * rc / ns ** 2
+            for ql, pl in ch:
+                U += 0.5 * ql * qim / np.linalg.norm(pl - sim)
+        return U
+
+    U_img = _richardson(images_self_energy, 0.02)
+    m = {"lj_types": {"eps": [], "sigma": []}, "xi": None, "eta": None, "lj": [], "charges": [],
+         "dipoles": [{"pos": (0, 0, 0), "axis": tuple(e), "mu": mu} for mu, e in dips], "quads": []}
+    n = 7
+    s = oracle.make_setup((BIG,) * 3, rc, eps_rf=math.inf)
+    assert oracle.lrc(m, s, n)[2] == pytest.approx(n * U_img, rel=1e-8)
+
+
+def test_reaction_field_self_energy_hand_values():
+    """The self term for one point dipole mu per molecule: -N mu^2 / (2 rc^3)
+    at eps_RF = inf, nothing at eps_RF = 1 (no continuum), and the Onsager
+    factor 2 (eps - 1) / (2 eps + 1) of the cavity field in between; two
+    dipoles of one molecule enter through their vector sum (antiparallel
+    equal dipoles cancel)."""
+    rc, n, mu = 2.5, 10, 1.3
+    one = {"lj_types": {"eps": [], "sigma": []}, "xi": None, "eta": None, "lj": [], "charges": [],
+           "dipoles": [{"pos": (0.2, 0, 0), "axis": (0, 0, 1), "mu": mu}], "quads": []}
+    box = (BIG,) * 3
+    assert oracle.lrc(one, oracle.make_setup(box, rc, eps_rf=math.inf), n)[2] == pytest.approx(
+        -n * mu * mu / (2 * rc ** 3), rel=1e-14)
+    assert oracle.lrc(one, oracle.make_setup(box, rc, eps_rf=1.0), n)[2] == 0.0
+    for eps in (2.0, 8.0, 80.0):
+        f = 2 * (eps - 1) / (2 * eps + 1)
+        assert oracle.lrc(one, oracle.make_setup(box, rc, eps_rf=eps), n)[2] == pytest.approx(
+            -f * n * mu * mu / (2 * rc ** 3), rel=1e-14)
+    anti = copy.deepcopy(one)
+    anti["dipoles"].append({"pos": (-0.2, 0, 0), "axis": (0, 0, -1), "mu": mu})
+    assert oracle.lrc(anti, oracle.make_setup(box, rc, eps_rf=math.inf), n)[2] == 0.0
+    perp = copy.deepcopy(one)
+    perp["dipoles"].append({"pos": (-0.2, 0, 0), "axis": (1, 0, 0), "mu": 0.5})
+    assert oracle.lrc(perp, oracle.make_setup(box, rc, eps_rf=math.inf), n)[2] == pytest.approx(
+        -n * (mu * mu + 0.25) / (2 * rc ** 3), rel=1e-14)
+
+
 def test_reaction_field_vacuum_vanishes_and_no_force():
     """eps_RF = 1 (no dielectric continuum) gives no reaction field; the RF
     term never changes forces, only energy and torques."""
@@ -426,6 +483,29 @@ def test_brute_force_equals_linked_cells(which):
     assert oc["U"] == pytest.approx(ob["U"], rel=1e-12)
     assert oc["W"] == pytest.approx(ob["W"], rel=1e-12)
     assert oc["n_mol_pairs"] == ob["n_mol_pairs"]
+
+
+@pytest.mark.parametrize("which", ["2cljq", "4site"])
+def test_forces_subset_equals_full_evaluation(which):
+    """orc_forces_subset (the checker of sampled parity on systems too large
+    for a full evaluation) returns, for each selected molecule in selection
+    order, exactly the row of the full linked-cell evaluation; selections
+    include molecules in the first and last cells (periodic neighbours),
+    repeats and an unsorted order."""
+    cfg = mdgen.config_2cljq(n=1500) if which == "2cljq" else mdgen.config_4site(n=900)
+    s = oracle.setup_from_config(cfg)
+    F, tau, _ = oracle.forces(cfg["model"], s, cfg["r"], cfg["q"], use_cells=True)
+    r = cfg["r"]
+    L = np.asarray(cfg["box"])
+    edge = np.where(((r % L) < 0.5).any(axis=1) | ((r % L) > L - 0.5).any(axis=1))[0]
+    rng = np.random.default_rng(5)
+    sel = np.concatenate([edge[:20], rng.choice(r.shape[0], 40, replace=False), edge[:3], [0, r.shape[0] - 1, 0]])
+    rng.shuffle(sel)
+    Fs, ts = oracle.forces_subset(cfg["model"], s, cfg["r"], cfg["q"], sel)
+    assert Fs.shape == (sel.shape[0], 3) and ts.shape == (sel.shape[0], 3)
+    scF, sct = np.abs(F).max(), np.abs(tau).max()
+    assert np.allclose(Fs, F[sel], rtol=0, atol=1e-14 * scF)
+    assert np.allclose(ts, tau[sel], rtol=0, atol=1e-14 * sct)
 
 
 # ------------------------------------------------------- hit ratio (§3)

@@ -1,7 +1,9 @@
 """md_kinetic_noalloc (the allocation-free kinetic-energy entry point) must
 return what md_energy_virial reports for the same state, on two calls in a
-row.  This file is collected last so that a failure here cannot stop the
-other GPU tests from running."""
+row, agree with the FP64 oracle's kinetic energies, and leave the free
+device memory unchanged (it promises to allocate nothing).  This file is
+collected last so that a failure here cannot stop the other GPU tests from
+running."""
 import numpy as np
 import pytest
 
@@ -14,6 +16,8 @@ from paper_1408_4599_gb300 import md  # noqa: E402
 
 
 def test_kinetic_noalloc_matches_energy_virial():
+    import oracle
+
     dev = torch.device("cuda:0")
     cfg = mdgen.config_2cljq(n=5000)
     sysm = md.System(cfg)
@@ -22,22 +26,31 @@ def test_kinetic_noalloc_matches_energy_virial():
     K_out = torch.zeros(2, dtype=torch.float64, device=dev)
     mass = mdgen.model_mass(cfg["model"])
     moments = mdgen.model_principal_moments(cfg["model"])
+    n = cfg["r"].shape[0]
+    r, v, q, j = (torch.zeros((n, w), dtype=torch.float64, device=dev) for w in (3, 3, 4, 3))
+    F = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    tau = torch.zeros_like(F)
     for call in range(2):
         sysm.step(3, cfg["dt"])
         obs = sysm.observables()
-        n = cfg["r"].shape[0]
-        r, v, q, j = (torch.zeros((n, w), dtype=torch.float64, device=dev) for w in (3, 3, 4, 3))
         sysm.molecules(r=r, v=v, q=q, j=j)
-        F = torch.zeros((n, 3), dtype=torch.float64, device=dev)
-        tau = torch.zeros_like(F)
         sysm.forces(F=F, tau=tau)
         K_out.fill_(-1.0)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info(dev)[0]
         md.md_kinetic_noalloc(v, q, j, F, tau, mass, moments, cfg["dt"], K_out)
         torch.cuda.synchronize()
+        free_after = torch.cuda.mem_get_info(dev)[0]
+        assert free_after == free_before, (call, free_before - free_after)
         kt, kr = K_out.cpu().tolist()
         assert kt == pytest.approx(obs["K_trans"], rel=1e-12), call
         assert kr == pytest.approx(obs["K_rot"], rel=1e-12), call
         assert kt > 0 and kr > 0
+        # the FP64 oracle on the same half-step state (the rotational energy
+        # is formed in FP32 per molecule on the GPU)
+        ok_t, ok_r = oracle.kinetic(cfg["model"], cfg["dt"], *(x.cpu().numpy() for x in (v, q, j, F, tau)))
+        assert kt == pytest.approx(ok_t, rel=1e-12), call
+        assert kr == pytest.approx(ok_r, rel=1e-6), call
     sysm.close()
 
 
