@@ -85,6 +85,7 @@ struct AdjExtra {
 template <class SIG, bool HALF>
 struct AdjOp {
     static constexpr int IMAX = 32;
+    static constexpr bool RUNS = false;
     using Tile = WarpTile<AdjExtra>;
     using LY = AdjLayout<SIG>;
     static constexpr int S = SIG::S;
@@ -145,9 +146,12 @@ struct AdjOp {
                 const bool lj = (ra & ROLE_LJ) && (rb & ROLE_LJ);
                 const bool el = (ra & EL_ROLES) && (rb & EL_ROLES);
                 if (!lj && !el) continue;
-                const float x = X0 + I.d[a][0] - db.x;
-                const float y = X1 + I.d[a][1] - db.y;
-                const float z = X2 + I.d[a][2] - db.z;
+                float da0, da1, da2;
+                float4 ea;
+                imol_site<SIG>(m, I, a, da0, da1, da2, ea);
+                const float x = X0 + da0 - db.x;
+                const float y = X1 + da1 - db.y;
+                const float z = X2 + da2 - db.z;
                 const float r2 = x * x + y * y + z * z;
                 const float Xx = X0 * x + X1 * y + X2 * z;
                 if (lj) {
@@ -172,7 +176,6 @@ struct AdjOp {
                 if (el) {
                     const float ir = rsqrtf(r2);
                     const float xh = x * ir, yh = y * ir, zh = z * ir;
-                    const float4 &ea = I.e[a];
                     const bool axa = (ra & AX_ROLES) != 0, axb = (rb & AX_ROLES) != 0;
                     const float pa = axa ? (ea.x * xh + ea.y * yh + ea.z * zh) : 0.f;
                     const float pb = axb ? (eb.x * xh + eb.y * yh + eb.z * zh) : 0.f;

@@ -228,8 +228,7 @@ __global__ void __launch_bounds__(MD_WARPS * 32) k_force_batch(const __grid_cons
                 B.cellN[2 * c] = nm;
                 B.cellN[2 * c + 1] = ne;
             }
-            op.sU = op.kU = op.sW = op.kW = op.sX = op.kX = op.sY = op.kY = op.sZ = op.kZ = 0.f;
-            op.nmol = op.nexam = 0;
+            op.reset_totals();
         }
     }
 }

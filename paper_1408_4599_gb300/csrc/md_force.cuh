@@ -34,17 +34,16 @@ namespace {
 
 using namespace mdk;
 
-// Resident blocks the register budget is sized for: 5 blocks of 4 warps (at
-// most 102 registers) for the half shell of models of up to 3 merged sites
-// without a dipole; 4 (128) for their full shell (its segmented i sums and
-// FP64 stores ran 10% slower under the tighter cap) and for the 3-site
-// models with a dipole, whose dipole terms spill at 102; 3 (168) for the
-// larger compiled signatures, whose site loops spill at 128 registers; 2 for
-// the run-time signature.
+// Resident blocks the register budget is sized for: 4 blocks of 4 warps (at
+// most 128 registers) for models of up to 3 merged sites (the run-drained
+// half shell keeps its i molecule and i sums in registers across the run and
+// spills under the 102-register cap of 5 blocks; 3 blocks measured 8% slower
+// on the 2CLJQ fluid); 3 (168) for the larger compiled signatures, whose
+// site loops spill at 128 registers; 2 for the run-time signature.
 template <class SIG, bool HALF>
 constexpr int force_min_blocks()
 {
-    return SIG::DYN ? 2 : (SIG::S > 3 ? 3 : ((!HALF || sig_has_role(SIG::ROLES, SIG::S, ROLE_DIP)) ? 4 : 5));
+    return SIG::DYN ? 2 : (SIG::S > 3 ? 3 : 4);
 }
 
 // Dynamic shared memory of one block: the warps' tiles, then (M = 2) their
@@ -90,7 +89,7 @@ __global__ void __launch_bounds__(MD_WARPS * 32, force_min_blocks<SIG, HALF>()) 
 
     // block partials: FP32 warp sums of the compensated lane sums; FP64 only
     // once per value per block
-    float v[5] = {op.sU - op.kU, op.sW - op.kW, op.sX - op.kX, op.sY - op.kY, op.sZ - op.kZ};
+    float v[5] = {op.total(0), op.total(1), op.total(2), op.total(3), op.total(4)};
     for (int q = 0; q < 5; q++)
         for (int msk = 16; msk > 0; msk >>= 1) v[q] += __shfl_xor_sync(FULLMASK, v[q], msk);
     const int wm = __reduce_add_sync(FULLMASK, op.nmol), we = __reduce_add_sync(FULLMASK, op.nexam);

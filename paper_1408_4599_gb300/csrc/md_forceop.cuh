@@ -31,16 +31,23 @@ struct ForceArgs {
 template <class SIG, int M>
 cudaError_t launch_force_sig(const ForceArgs &A, int half_shell, int n_blocks, cudaStream_t s);
 
+struct ForceExtraHalf {
+    float tot[10][32];  // per lane: compensated totals (sum, compensation) of U, W, W_xx, W_yy, W_zz
+};
 struct ForceExtra {
-    float4 if4[32];  // i totals of the pass: F, tau_x
-    float2 it2[32];  // tau_y, tau_z
+    float4 if4[32];     // i totals of the pass (full shell): F, tau_x
+    float2 it2[32];     // tau_y, tau_z
+    float tot[10][32];
 };
 
 template <class SIG, bool HALF>
 struct ForceOp {
     static constexpr int IMAX = 32;
     static constexpr int NQ = SIG::SINGLE ? 3 : 6;  // accumulated values per molecule: F, and tau unless single-site
-    using Tile = WarpTile<ForceExtra>;
+    // the half shell is drained in runs (drain): a lane keeps its i's force
+    // and torque in registers over consecutive pairs of that i
+    static constexpr bool RUNS = HALF;
+    using Tile = std::conditional_t<HALF, WarpTileD<ForceExtraHalf, QRUN>, WarpTile<ForceExtra, QCAP>>;
     const DevModel &m;
     const ForceArgs &A;
     int K;
@@ -49,19 +56,29 @@ struct ForceOp {
     float tq0, tq1, tq2;                           // its torque on j (half shell)
     int pjs, psi;                                  // storage slots of its j and i
     float cU, cW, cX, cY, cZ;                      // pass sums of energy and virial (FP32)
-    float sU, kU, sW, kW, sX, kX, sY, kY, sZ, kZ;  // compensated lane totals
     int nmol, nexam;
     Tile *T;
+    int ln;                                        // the lane (index of its compensated totals)
 
+    // The compensated lane totals live in shared memory (T->x.tot), updated
+    // once per pass, which keeps ten registers free for the pair math.
     __device__ ForceOp(const DevModel &m_, const ForceArgs &A_, int K_, Tile *T_) : m(m_), A(A_), K(K_), T(T_)
     {
-        sU = kU = sW = kW = sX = kX = sY = kY = sZ = kZ = 0.f;
+        ln = threadIdx.x & 31;
+        reset_totals();
+    }
+    __device__ void reset_totals()
+    {
+#pragma unroll
+        for (int q = 0; q < 10; q++) T->x.tot[q][ln] = 0.f;
         nmol = nexam = 0;
     }
+    // the lane's total of value q (0 U, 1 W, 2 W_xx, 3 W_yy, 4 W_zz)
+    __device__ float total(int q) const { return T->x.tot[2 * q][ln] - T->x.tot[2 * q + 1][ln]; }
     __device__ void pass_begin(int ig_, int ni, int lane)
     {
         ig = ig_;
-        if (!HALF) {  // the half shell adds its i terms per pair (chunk_end)
+        if constexpr (!HALF) {  // the half shell sums its i terms while draining
             for (int t = lane; t < ni; t += 32) {
                 T->x.if4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
                 T->x.it2[t] = make_float2(0.f, 0.f);
@@ -95,26 +112,13 @@ struct ForceOp {
             tq2 = tq[2];
         }
     }
-    // End of a chunk.  Half shell: each lane adds its pair's terms straight
-    // to the FP32 accumulator records of i and j (one 16-byte vector
-    // reduction for F and one for tau per molecule; measured faster than
-    // per-candidate shared accumulators for the Newton-3 side and than a
-    // segmented warp sum for the i side).  Full shell (deterministic): a
-    // segmented suffix sum over the lanes, the first lane of each i adding the
-    // i's total to the pass totals in shared memory.
+    // End of a chunk (full shell, deterministic; the half shell is drained
+    // in runs): a segmented suffix sum over the lanes, the first lane of each
+    // i adding the i's total to the pass totals in shared memory.
     __device__ void chunk_end(Tile &, int il, int, bool valid, int lane)
     {
-        if (HALF) {
-            if (valid) {
-                float *a = A.acc + (long long)FACC_STRIDE * psi;
-                red_add_v4(a, pF0, pF1, pF2, 0.f);
-                if (NQ == 6) red_add_v4(a + 4, pT0, pT1, pT2, 0.f);
-                float *b = A.acc + (long long)FACC_STRIDE * pjs;
-                red_add_v4(b, -pF0, -pF1, -pF2, 0.f);
-                if (NQ == 6) red_add_v4(b + 4, tq0, tq1, tq2, 0.f);
-            }
-            return;
-        }
+        if constexpr (HALF) return;
+        else {
         const int nvalid = __popc(__ballot_sync(FULLMASK, valid));  // valid lanes are a prefix
         const int prev = __shfl_up_sync(FULLMASK, il, 1);
         const bool head = valid && (lane == 0 || prev != il);
@@ -146,11 +150,87 @@ struct ForceOp {
             }
             T->x.if4[il] = a;
         }
+        }
+    }
+    // Half shell, run-drained: the queue's qn entries are split into 32
+    // contiguous runs of R entries, one per lane (R odd: the lanes'
+    // shared-memory reads of one step fall in distinct banks).  Every pair
+    // adds its Newton-3 reaction (-F, tau_j) straight to the j record; the i
+    // side is summed in registers while the run's i stays the same and added
+    // to the i record when it changes (entries of one i are contiguous), so
+    // the i records see ~1/R of the per-pair reductions and the i molecule
+    // is loaded once per run segment.
+    struct Run {
+        int cur;
+        IMol<SIG> I;
+        float a[6];
+    };
+    template <class Exact>
+    __device__ __forceinline__ void run_step(Tile &Tl, Run &r, int e, int sbase, Exact &exact, float band_lo)
+    {
+        const int q = Tl.queue[e];
+        const int il = q >> 16, k = q & 0xffff;
+        if (il != r.cur) {
+            if (r.cur >= 0) flush_i(sbase + r.cur, r.a);
+            r.cur = il;
+#pragma unroll
+            for (int c = 0; c < 6; c++) r.a[c] = 0.f;
+            if constexpr (SIG::LIN || SIG::SINGLE) load_i<SIG>(m, A.com, A.geo, K, sbase + il, r.I);
+        }
+        // models with per-site geometry reload it per pair (L1 hits) rather
+        // than hold it across the run
+        if constexpr (!(SIG::LIN || SIG::SINGLE)) load_i<SIG>(m, A.com, A.geo, K, sbase + il, r.I);
+        const float4 cj = Tl.cand(k);
+        const float X0 = r.I.c.x - cj.x, X1 = r.I.c.y - cj.y, X2 = r.I.c.z - cj.z;
+        const int js = Tl.cand_slot(k);
+        float Fp[3], tp[3], tq[3], Up;
+        mol_pair<SIG, true>(m, X0, X1, X2, r.I, A.geo + (long long)js * K, Fp, tp, tq, Up);
+        // queued inside the FP32 band around r_c^2: the FP64 test decides
+        // (after the pair terms, so that no branch holds back their loads;
+        // a pair outside the cut-off is dropped)
+        if (Tile::DUP && X0 * X0 + X1 * X1 + X2 * X2 > band_lo && !exact(il, k)) return;
+        r.a[0] += Fp[0];
+        r.a[1] += Fp[1];
+        r.a[2] += Fp[2];
+        if (NQ == 6) {
+            r.a[3] += tp[0];
+            r.a[4] += tp[1];
+            r.a[5] += tp[2];
+        }
+        cU += Up;
+        cW += X0 * Fp[0] + X1 * Fp[1] + X2 * Fp[2];
+        cX += X0 * Fp[0];
+        cY += X1 * Fp[1];
+        cZ += X2 * Fp[2];
+        nmol++;
+        float *b = A.acc + (long long)FACC_STRIDE * js;
+        red_add_v4(b, -Fp[0], -Fp[1], -Fp[2], 0.f);
+        if (NQ == 6) red_add_v4(b + 4, tq[0], tq[1], tq[2], 0.f);
+    }
+    template <class Exact>
+    __device__ void drain(Tile &Tl, int qn, int sbase, int lane, Exact &exact, float band_lo)
+    {
+        const int R = ((qn + 31) >> 5) | 1;
+        const int e0 = lane * R, e1 = min(e0 + R, qn);
+        Run r;
+        r.cur = -1;
+        r.I.slot = 0;
+#pragma unroll
+        for (int c = 0; c < 6; c++) r.a[c] = 0.f;
+        for (int t = 0; t < R; t++)  // warp-uniform trip count
+            if (e0 + t < e1) run_step(Tl, r, e0 + t, sbase, exact, band_lo);
+        if (r.cur >= 0) flush_i(sbase + r.cur, r.a);
+    }
+    __device__ __forceinline__ void flush_i(int si, const float (&v)[6])
+    {
+        float *a = A.acc + (long long)FACC_STRIDE * si;
+        red_add_v4(a, v[0], v[1], v[2], 0.f);
+        if (NQ == 6) red_add_v4(a + 4, v[3], v[4], v[5], 0.f);
     }
     __device__ void seg_end(Tile &, int, int) {}
     __device__ void pass_end(int s0, int ig_, int ni, int lane)
     {
-        if (!HALF) {
+        if constexpr (!HALF) {
             for (int t = lane; t < ni; t += 32) {
                 const int si = s0 + ig_ + t;
                 const float4 i4 = T->x.if4[t];
@@ -175,11 +255,14 @@ struct ForceOp {
                 }
             }
         }
-        kahan_add(sU, kU, cU);
-        kahan_add(sW, kW, cW);
-        kahan_add(sX, kX, cX);
-        kahan_add(sY, kY, cY);
-        kahan_add(sZ, kZ, cZ);
+        const float c5[5] = {cU, cW, cX, cY, cZ};
+#pragma unroll
+        for (int q = 0; q < 5; q++) {
+            float sq = T->x.tot[2 * q][ln], kq = T->x.tot[2 * q + 1][ln];
+            kahan_add(sq, kq, c5[q]);
+            T->x.tot[2 * q][ln] = sq;
+            T->x.tot[2 * q + 1][ln] = kq;
+        }
     }
 };
 
@@ -189,11 +272,8 @@ struct ForceOp {
 template <class Op>
 __device__ __forceinline__ void op_warp_totals(Op &op, float (&v)[5], int &nm, int &ne)
 {
-    v[0] = op.sU - op.kU;
-    v[1] = op.sW - op.kW;
-    v[2] = op.sX - op.kX;
-    v[3] = op.sY - op.kY;
-    v[4] = op.sZ - op.kZ;
+#pragma unroll
+    for (int q = 0; q < 5; q++) v[q] = op.total(q);
     for (int q = 0; q < 5; q++)
         for (int msk = 16; msk > 0; msk >>= 1) v[q] += __shfl_xor_sync(FULLMASK, v[q], msk);
     nm = __reduce_add_sync(FULLMASK, op.nmol);

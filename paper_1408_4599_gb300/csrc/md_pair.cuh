@@ -296,13 +296,21 @@ __device__ __forceinline__ void elec_site(const int ra, const int rb, const floa
     }
 }
 
-// The i molecule of the current traversal step, in registers.
-template <class SIG>
+// The i molecule of the current traversal step, in registers.  Linear
+// molecules keep only their axis u (site offsets z_a u and axes +-u are
+// formed per pair), so that an i held across many pairs costs few registers.
+template <class SIG, bool LIN = SIG::LIN>
 struct IMol {
     float4 c;                 // centre of mass (cell-centre frame)
     float d[SIG::S][3];       // space-frame site offsets
     float4 e[SIG::S];         // space-frame axes
-    float4 e_axis;            // linear molecules: the molecular axis u
+    float4 e_axis;            // unused
+    int slot;
+};
+template <class SIG>
+struct IMol<SIG, true> {
+    float4 c;                 // centre of mass (cell-centre frame)
+    float4 e_axis;            // the molecular axis u
     int slot;
 };
 
@@ -313,17 +321,7 @@ __device__ __forceinline__ void load_i(const DevModel &m, const float4 *com, con
     I.slot = si;
     I.c = com[si];
     if constexpr (SIG::LIN) {
-        const float4 u = geo[(long long)si * K];
-        I.e_axis = u;
-#pragma unroll
-        for (int a = 0; a < SIG::S; a++) {
-            const float z = m.body[a][2], sa = m.axis[a][2];
-            I.d[a][0] = z * u.x;
-            I.d[a][1] = z * u.y;
-            I.d[a][2] = z * u.z;
-            I.e[a] = (SIG::role(a, m) & AX_ROLES) ? make_float4(sa * u.x, sa * u.y, sa * u.z, 0.f)
-                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        I.e_axis = geo[(long long)si * K];
     } else {
 #pragma unroll
         for (int a = 0; a < SIG::S; a++) {
@@ -340,6 +338,64 @@ __device__ __forceinline__ void load_i(const DevModel &m, const float4 *com, con
     }
 }
 
+// Paired FP32 arithmetic of sm_100-class GPUs (fma/mul/add.rn.f32x2): two
+// independent FP32 operations per instruction on a register pair, the same
+// FMA throughput in half the issue slots.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// Linear two-centre models whose sites 0 and 1 are plain LJ centres of one
+// type (2CLJ, 2CLJQ, 2CLJDQ): their four LJ site pairs are evaluated as two
+// f32x2 pairs, P0 = (a0 b0, a1 b1) and P1 = (a0 b1, a1 b0), the low half
+// always on i's site 0 and the high half on i's site 1.
+template <class SIG>
+__host__ __device__ constexpr bool lin_lj2()
+{
+    return SIG::LIN && !SIG::DYN && SIG::S >= 2 && sig_role(SIG::ROLES, 0) == ROLE_LJ &&
+           sig_role(SIG::ROLES, 1) == ROLE_LJ;
+}
+
+// Eq. 1 on two site pairs at once: x, y, z hold the two site-site vectors
+// (i site minus j site); the force on the i sites is added to fx, fy, fz and
+// the unshifted energy to U.
+__device__ __forceinline__ void lj_pair2(const float2 x, const float2 y, const float2 z, const float2 sig2,
+                                         const float2 eps4, const float2 eps24, float2 &fx, float2 &fy, float2 &fz,
+                                         float2 &U)
+{
+    const float2 r2 = fma2(z, z, fma2(y, y, mul2(x, x)));
+    const float2 ir2 = f2(__fdividef(1.f, r2.x), __fdividef(1.f, r2.y));
+    const float2 s2 = mul2(sig2, ir2);
+    const float2 s6 = mul2(mul2(s2, s2), s2);
+    const float2 fr = mul2(mul2(mul2(eps24, s6), fma2(s6, f2(2.f, 2.f), f2(-1.f, -1.f))), ir2);
+    U = fma2(eps4, fma2(s6, s6, f2(-s6.x, -s6.y)), U);
+    fx = fma2(fr, x, fx);
+    fy = fma2(fr, y, fy);
+    fz = fma2(fr, z, fz);
+}
+
+// Site a of the i molecule: space-frame offset d and axis e (zero unless
+// the site carries an axis).
+template <class SIG>
+__device__ __forceinline__ void imol_site(const DevModel &m, const IMol<SIG> &I, int a, float &d0, float &d1,
+                                          float &d2, float4 &e)
+{
+    if constexpr (SIG::LIN) {
+        const float4 u = I.e_axis;
+        const float z = m.body[a][2], sa = m.axis[a][2];
+        d0 = z * u.x;
+        d1 = z * u.y;
+        d2 = z * u.z;
+        e = (SIG::role(a, m) & AX_ROLES) ? make_float4(sa * u.x, sa * u.y, sa * u.z, 0.f)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        d0 = I.d[a][0];
+        d1 = I.d[a][1];
+        d2 = I.d[a][2];
+        e = I.e[a];
+    }
+}
+
 // Pair of molecules: force on i, torque on i (lever arms + orientation),
 // energy; with JSIDE also the torque on j from the pair's angular-momentum
 // balance, tau_i + tau_j + X x F_ij = 0 (X = R_i - R_j), which holds exactly
@@ -353,17 +409,20 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
 {
     constexpr int S = SIG::S;
     float fa[S][3], xa[S][3];
+    float4 ea[S];  // space-frame axes of i's sites
 #pragma unroll
     for (int a = 0; a < S; a++) {
         fa[a][0] = fa[a][1] = fa[a][2] = 0.f;
+        float d0, d1, d2;
+        imol_site<SIG>(m, I, a, d0, d1, d2, ea[a]);
         if (SIG::at_com(a)) {  // zero offset: no add (x + 0 is not folded under IEEE rules)
             xa[a][0] = X0;
             xa[a][1] = X1;
             xa[a][2] = X2;
         } else {
-            xa[a][0] = X0 + I.d[a][0];
-            xa[a][1] = X1 + I.d[a][1];
-            xa[a][2] = X2 + I.d[a][2];
+            xa[a][0] = X0 + d0;
+            xa[a][1] = X1 + d1;
+            xa[a][2] = X2 + d2;
         }
     }
     float ti[3] = {0.f, 0.f, 0.f}, tdummy[3];
@@ -381,6 +440,28 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
     } else {
         float4 uj = make_float4(0.f, 0.f, 0.f, 0.f);
         if constexpr (SIG::LIN) uj = __ldg(gj);  // the j molecule's axis
+        if constexpr (lin_lj2<SIG>()) {
+            // x_ab = X + z_a u_i - z_b u_j for the LJ sites a, b in {0, 1}
+            const float4 ui = I.e_axis;
+            const float z0 = m.body[0][2], z1 = m.body[1][2];
+            const float2 za = f2(z0, z1), nzb0 = f2(-z0, -z1), nzb1 = f2(-z1, -z0);
+            const float2 wx = fma2(za, f2(ui.x, ui.x), f2(X0, X0));
+            const float2 wy = fma2(za, f2(ui.y, ui.y), f2(X1, X1));
+            const float2 wz = fma2(za, f2(ui.z, ui.z), f2(X2, X2));
+            const float2 ujx = f2(uj.x, uj.x), ujy = f2(uj.y, uj.y), ujz = f2(uj.z, uj.z);
+            const float2 sg = f2(m.sig2[0][0], m.sig2[0][0]), e4 = f2(m.eps4[0][0], m.eps4[0][0]),
+                         e24 = f2(m.eps24[0][0], m.eps24[0][0]);
+            float2 fx = f2(0.f, 0.f), fy = fx, fz = fx, U2 = fx;
+            lj_pair2(fma2(nzb0, ujx, wx), fma2(nzb0, ujy, wy), fma2(nzb0, ujz, wz), sg, e4, e24, fx, fy, fz, U2);
+            lj_pair2(fma2(nzb1, ujx, wx), fma2(nzb1, ujy, wy), fma2(nzb1, ujz, wz), sg, e4, e24, fx, fy, fz, U2);
+            U += (U2.x + U2.y) - 4.f * m.ushift[0][0];
+            fa[0][0] = fx.x;
+            fa[0][1] = fy.x;
+            fa[0][2] = fz.x;
+            fa[1][0] = fx.y;
+            fa[1][1] = fy.y;
+            fa[1][2] = fz.y;
+        }
         // the run-time signature keeps its j-site loop rolled (its i-site
         // loop stays unrolled, so the site totals stay in registers): a fully
         // unrolled 8 x 8 site loop with run-time roles takes minutes to compile
@@ -400,7 +481,7 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
 #pragma unroll
             for (int a = 0; a < S; a++) {
                 const int ra = SIG::role(a, m);
-                const bool lj = (ra & ROLE_LJ) && (rb & ROLE_LJ);
+                const bool lj = (ra & ROLE_LJ) && (rb & ROLE_LJ) && !(lin_lj2<SIG>() && a < 2 && b < 2);
                 const bool el = (ra & EL_ROLES) && (rb & EL_ROLES);
                 if (!lj && !el) continue;
                 const bool zb = SIG::LIN && SIG::at_com(b);
@@ -428,7 +509,7 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
                 }
                 if (el) {
                     elec_site<false>(ra, rb, m.chg[a], m.mu[a], m.Q[a], m.chg[b], m.mu[b], m.Q[b], m.frf, x, y, z,
-                                     ir, I.e[a], eb, U, fx, fy, fz, ti, tdummy);
+                                     ir, ea[a], eb, U, fx, fy, fz, ti, tdummy);
                 }
                 fa[a][0] += fx;
                 fa[a][1] += fy;
@@ -462,7 +543,7 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
             F0 += fa[a][0];
             F1 += fa[a][1];
             F2 += fa[a][2];
-            if (!SIG::SINGLE) {
+            if constexpr (!SIG::SINGLE && !SIG::LIN) {
                 ti[0] += I.d[a][1] * fa[a][2] - I.d[a][2] * fa[a][1];
                 ti[1] += I.d[a][2] * fa[a][0] - I.d[a][0] * fa[a][2];
                 ti[2] += I.d[a][0] * fa[a][1] - I.d[a][1] * fa[a][0];
@@ -504,7 +585,8 @@ constexpr int JCAP = MD_JCAP;  // staged candidates per segment (a multiple of 3
 #define MD_TEST_UNROLL 8
 #endif
 constexpr int NTEST = MD_TEST_UNROLL;   // candidates per lane per test round
-constexpr int QCAP = 32 * (NTEST + 1);  // hit queue (31 waiting + NTEST x 32 new)
+constexpr int QCAP = 32 * (NTEST + 1);  // hit queue of chunk-drained operations (31 waiting + NTEST x 32 new)
+constexpr int QRUN = 1024;              // hit queue of run-drained operations (a window's hits, or a part)
 
 // Stencils wider than a warp (M = 2): each stencil cell's first slot and
 // the exclusive prefix of the counts, per warp in shared memory.
@@ -513,13 +595,65 @@ struct StencilMeta {
     int pre[Stencil<2>::FULL + 1];
 };
 
-// Per-warp staging area; Extra is the pair operation's own shared state.
-template <class Extra>
+// Per-warp staging area; Extra is the pair operation's own shared state, QC
+// the capacity of its hit queue.
+template <class Extra, int QC = QCAP>
 struct WarpTile {
+    static constexpr int QCAPACITY = QC;
+    static constexpr bool DUP = false;
     float4 jc[JCAP];          // candidate COM + image offset (i-cell frame); w = storage slot bits
     unsigned char jst[JCAP];  // stencil index of the candidate's cell
-    int queue[QCAP];
+    int queue[QC];
     Extra x;
+    __device__ __forceinline__ float4 cand(int k) const { return jc[k]; }
+    __device__ __forceinline__ int cand_slot(int k) const { return __float_as_int(jc[k].w); }
+    __device__ __forceinline__ void stage(int t, float x_, float y_, float z_, int js, int o)
+    {
+        jc[t] = make_float4(x_, y_, z_, __int_as_float(js));
+        jst[t] = (unsigned char)o;
+    }
+    // duplicated layout (WarpTileD only)
+    __device__ __forceinline__ float4 dxy(int) const { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ __forceinline__ float2 dz(int) const { return make_float2(0.f, 0.f); }
+    __device__ __forceinline__ void pad(int, int) {}
+};
+
+// Staging area of the half shell's duplicated-candidate test: each
+// candidate's coordinates negated and duplicated, (-x, -x, -y, -y) and
+// (-z, -z), so that one f32x2 instruction advances the tests of two i
+// molecules against it, and 32 far-away sentinels after the window's last
+// candidate, so that test rounds need no range check.
+template <class Extra, int QC>
+struct WarpTileD {
+    static constexpr int QCAPACITY = QC;
+    static constexpr bool DUP = true;
+    float4 jd[JCAP + 32];
+    float2 jz[JCAP + 32];
+    int jslot[JCAP];          // storage slot of each candidate
+    unsigned char jst[JCAP];  // stencil index of the candidate's cell
+    int queue[QC];
+    Extra x;
+    __device__ __forceinline__ float4 cand(int k) const
+    {
+        const float4 d = jd[k];
+        return make_float4(-d.x, -d.z, -jz[k].x, 0.f);
+    }
+    __device__ __forceinline__ int cand_slot(int k) const { return jslot[k]; }
+    __device__ __forceinline__ void stage(int t, float x_, float y_, float z_, int js, int o)
+    {
+        jd[t] = make_float4(-x_, -x_, -y_, -y_);
+        jz[t] = make_float2(-z_, -z_);
+        jslot[t] = js;
+        jst[t] = (unsigned char)o;
+    }
+    __device__ __forceinline__ float4 dxy(int k) const { return jd[k]; }
+    __device__ __forceinline__ float2 dz(int k) const { return jz[k]; }
+    // sentinels at candidates [nj, nj + 32) (all lanes call)
+    __device__ __forceinline__ void pad(int nj, int lane)
+    {
+        jd[nj + lane] = make_float4(-1.0e18f, -1.0e18f, -1.0e18f, -1.0e18f);
+        jz[nj + lane] = make_float2(-1.0e18f, -1.0e18f);
+    }
 };
 
 // The periodic grid a cell belongs to (one system, or one replica of a batch).
@@ -576,11 +710,17 @@ __device__ __forceinline__ void for_each_cell(long long ncell, int parts, unsign
 //                                     (lanes of one i are contiguous and
 //                                     their k are distinct)
 //   count_examined(n)
+// An operation with RUNS = true is instead drained in runs: the hits of all
+// i's of a pass against the staged window collect in its (larger) queue and
+// drain(T, qn, sbase, lane) consumes them at the end of the window (or when
+// the queue would overflow); lanes take contiguous runs of entries, so that
+// a lane meets one i for many consecutive pairs (sbase = storage slot of
+// the pass's first i).  chunk_end is then not called.
 // cell_start holds global slots; c is the cell index inside the grid.
-template <class SIG, bool HALF, int M = 1, class Op, class Extra>
+template <class SIG, bool HALF, int M = 1, class Op, class Tile>
 __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView &g, const int *__restrict__ cell_start,
                                               const float4 *__restrict__ com, const float4 *__restrict__ geo,
-                                              const double *__restrict__ r64, int K, long long c, WarpTile<Extra> &T,
+                                              const double *__restrict__ r64, int K, long long c, Tile &T,
                                               Op &op, int lane, StencilMeta *meta = nullptr, int part = 0,
                                               int parts = 1)
 {
@@ -627,6 +767,8 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
         self_cnt = __shfl_sync(FULLMASK, t_cnt, SELF);
         // the i-cell is the stencil's own entry (no separate load round)
         s0 = __shfl_sync(FULLMASK, t_j0, SELF);
+        // the table staging reads (shared memory, so that it holds no
+        // registers while the pairs are computed); unused entries never match
     } else {
         int carry = 0;
         for (int e0 = 0; e0 < NOFF; e0 += 32) {  // warp-uniform
@@ -680,8 +822,8 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
             if (valid) {
                 IMol<SIG> I;
                 load_i<SIG>(m, com, geo, K, s0 + ig + il, I);
-                const float4 cj = T.jc[k];
-                op.pair(T, I, k, I.c.x - cj.x, I.c.y - cj.y, I.c.z - cj.z, __float_as_int(cj.w));
+                const float4 cj = T.cand(k);
+                op.pair(T, I, k, I.c.x - cj.x, I.c.y - cj.y, I.c.z - cj.z, T.cand_slot(k));
             }
             op.chunk_end(T, il, k, valid, lane);
         };
@@ -709,8 +851,7 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
                                 oz = __shfl_sync(FULLMASK, t_oz, o);
                     if (t < nj) {
                         const float4 cj = com[js];
-                        T.jc[t] = make_float4(cj.x + ox, cj.y + oy, cj.z + oz, __int_as_float(js));
-                        T.jst[t] = (unsigned char)o;
+                        T.stage(t, cj.x + ox, cj.y + oy, cj.z + oz, js, o);
                     }
                 }
             } else {
@@ -727,87 +868,196 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
                     stencil_offset<M>(HALF, o, dx, dy, dz);
                     const int js = meta->j0[o] + (x - meta->pre[o]);
                     const float4 cj = com[js];
-                    T.jc[t] = make_float4(cj.x + dx * g.ellf[0], cj.y + dy * g.ellf[1], cj.z + dz * g.ellf[2],
-                                          __int_as_float(js));
-                    T.jst[t] = (unsigned char)o;
+                    T.stage(t, cj.x + dx * g.ellf[0], cj.y + dy * g.ellf[1], cj.z + dz * g.ellf[2], js, o);
                 }
             }
+            T.pad(nj, lane);
             // the i-cell's entries in this window: local index self_lo + (k - self_base)
             const int w_lo = max(self_pre, seg0), w_hi = min(self_pre + self_cnt, seg0 + nj);
             const int self_n = max(0, w_hi - w_lo), self_lo = w_lo - self_pre, self_base = w_lo - seg0;
             op.seg_begin(T, nj, lane);
             __syncwarp();
+            // FP64 cut-off decision of the pass's i molecule il and staged
+            // candidate k (pairs queued inside the FP32 band)
+            auto exact_in = [&](int il, int k) -> bool {
+                int dx, dy, dz, kx, ky, kz;
+                stencil_offset<M>(HALF, T.jst[k], dx, dy, dz);
+                wrap_axis(cx, dx, g.nc[0], kx);
+                wrap_axis(cy, dy, g.nc[1], ky);
+                wrap_axis(cz, dz, g.nc[2], kz);
+                const double *ri = r64 + 3LL * (s0 + ig + il), *rj = r64 + 3LL * T.cand_slot(k);
+                const double e0 = __dsub_rn(__dsub_rn(ri[0], rj[0]), (double)kx * g.L[0]);
+                const double e1 = __dsub_rn(__dsub_rn(ri[1], rj[1]), (double)ky * g.L[1]);
+                const double e2 = __dsub_rn(__dsub_rn(ri[2], rj[2]), (double)kz * g.L[2]);
+                return __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2)) < g.rc2;
+            };
             int qn = 0;
-            for (int il = ig; il < ig + ni; il++) {
-                const int si = s0 + il;
-                const bool in_seg = self_n > 0 && il >= self_lo && il < self_lo + self_n;
-                const float4 ci = in_seg ? T.jc[self_base + il - self_lo] : com[si];
-                const int skip_to = (self_n > 0 && HALF) ? max(0, min(self_n, il - self_lo + 1)) : 0;
-                const int self_k = (!HALF && in_seg) ? self_base + (il - self_lo) : -1;
-                const int tag = (il - ig) << 16;
-                // squared COM distance of candidate k (huge if k is not a candidate of i)
-                auto dist2 = [&](int k) -> float {
-                    if (k >= nj || (!HALF && k == self_k)) return 3.0e38f;
-                    const float4 cj = T.jc[k];
-                    const float X0 = ci.x - cj.x, X1 = ci.y - cj.y, X2 = ci.z - cj.z;
-                    return X0 * X0 + X1 * X1 + X2 * X2;
-                };
-                // the same test in FP64 from the FP64 state (pairs near the cut-off)
-                auto test64 = [&](int k) -> bool {
-                    int dx, dy, dz, kx, ky, kz;
-                    stencil_offset<M>(HALF, T.jst[k], dx, dy, dz);
-                    wrap_axis(cx, dx, g.nc[0], kx);
-                    wrap_axis(cy, dy, g.nc[1], ky);
-                    wrap_axis(cz, dz, g.nc[2], kz);
-                    const double *ri = r64 + 3LL * si, *rj = r64 + 3LL * __float_as_int(T.jc[k].w);
-                    const double e0 = __dsub_rn(__dsub_rn(ri[0], rj[0]), (double)kx * g.L[0]);
-                    const double e1 = __dsub_rn(__dsub_rn(ri[1], rj[1]), (double)ky * g.L[1]);
-                    const double e2 = __dsub_rn(__dsub_rn(ri[2], rj[2]), (double)kz * g.L[2]);
-                    return __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2)) < g.rc2;
-                };
-                // one test round: NT candidates per lane (independent tests),
-                // then the hits are appended in candidate order
-                auto round = [&](auto ntc, int kb) {
-                    constexpr int NT = decltype(ntc)::value;
-                    bool h[NT], near[NT], any_near = false;
+            if constexpr (Tile::DUP) {
+                // two i molecules per test round (a = il, b = il + 1; b absent
+                // at an odd end of the pass) against candidates k = kb + 32 u
+                // + lane, with kb the i's first candidate rounded down to a
+                // multiple of 32 and as many 32-wide steps as reach the
+                // window's end (the sentinels fill the last step); tests
+                // against the widened bound rc^2 + band, the FP64 decision
+                // inside the band is taken when the pair is drained
+                static_assert(JCAP == 256, "the round widths below cover 1 ... 8 steps of 32");
+                const float hi = g.rc2f + g.bandf;
+                for (int il = ig; il < ig + ni; il += 2) {
+                    const bool has_b = il + 1 < ig + ni;
+                    const int ib = has_b ? il + 1 : il;
+                    auto ci_of = [&](int i) -> float4 {
+                        const bool in_seg = self_n > 0 && i >= self_lo && i < self_lo + self_n;
+                        return in_seg ? T.cand(self_base + i - self_lo) : com[s0 + i];
+                    };
+                    auto skip_of = [&](int i) -> int {
+                        return (self_n > 0 && HALF) ? max(0, min(self_n, i - self_lo + 1)) : 0;
+                    };
+                    const float4 ca = ci_of(il), cb = ci_of(ib);
+                    const int skip_a = skip_of(il), skip_b = has_b ? skip_of(ib) : nj;
+                    const float2 Cx = f2(ca.x, cb.x), Cy = f2(ca.y, cb.y), Cz = f2(ca.z, cb.z);
+                    const int kb = skip_a & ~31;
+                    const int tag_a = (il - ig) << 16, tag_b = (ib - ig) << 16;
+                    auto round_d = [&](auto ntc) {
+                        constexpr int NT = decltype(ntc)::value;
+                        bool ha[NT], hb[NT];
 #pragma unroll
-                    for (int u = 0; u < NT; u++) {
-                        const float d2 = dist2(kb + 32 * u + lane);
-                        h[u] = d2 < g.rc2f;
-                        near[u] = fabsf(d2 - g.rc2f) < g.bandf;
-                        any_near |= near[u];
-                    }
-                    if (__any_sync(FULLMASK, any_near)) {  // rare: decide in FP64
+                        for (int u = 0; u < NT; u++) {
+                            const int k = kb + 32 * u + lane;
+                            const float4 d = T.dxy(k);
+                            const float2 dd = T.dz(k);
+                            const float2 dx = __fadd2_rn(Cx, f2(d.x, d.y));
+                            const float2 dy = __fadd2_rn(Cy, f2(d.z, d.w));
+                            const float2 dz = __fadd2_rn(Cz, dd);
+                            const float2 d2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                            ha[u] = d2.x < hi;
+                            hb[u] = d2.y < hi;
+                        }
+                        // the own cell's candidates up to and including the i
+                        ha[0] = ha[0] && kb + lane >= skip_a;
+                        hb[0] = hb[0] && kb + lane >= skip_b;
 #pragma unroll
-                        for (int u = 0; u < NT; u++)
-                            if (near[u]) h[u] = test64(kb + 32 * u + lane);
-                    }
+                        for (int u = 0; u < NT; u++) {
+                            const unsigned bal = __ballot_sync(FULLMASK, ha[u]);
+                            if (ha[u]) T.queue[qn + __popc(bal & lt_mask)] = tag_a | (kb + 32 * u + lane);
+                            qn += __popc(bal);
+                        }
 #pragma unroll
-                    for (int u = 0; u < NT; u++) {
-                        const unsigned bal = __ballot_sync(FULLMASK, h[u]);
-                        if (h[u]) T.queue[qn + __popc(bal & lt_mask)] = tag | (kb + 32 * u + lane);
-                        qn += __popc(bal);
+                        for (int u = 0; u < NT; u++) {
+                            const unsigned bal = __ballot_sync(FULLMASK, hb[u] && has_b);
+                            if (hb[u] && has_b) T.queue[qn + __popc(bal & lt_mask)] = tag_b | (kb + 32 * u + lane);
+                            qn += __popc(bal);
+                        }
+                    };
+                    if (qn > Tile::QCAPACITY - 64 * (JCAP / 32)) {  // room for a full round of two i's
+                        __syncwarp();
+                        op.drain(T, qn, s0 + ig, lane, exact_in, g.rc2f - g.bandf);
+                        qn = 0;
+                        __syncwarp();
                     }
-                    while (qn >= 32) {
-                        __syncwarp();
-                        chunk(32);
-                        __syncwarp();
-                        for (int t = lane; t < qn - 32; t += 32) T.queue[t] = T.queue[32 + t];
-                        qn -= 32;
-                        __syncwarp();
+                    switch ((nj - kb + 31) >> 5) {  // warp-uniform, 1 ... JCAP / 32
+                    case 1: round_d(std::integral_constant<int, 1>{}); break;
+                    case 2: round_d(std::integral_constant<int, 2>{}); break;
+                    case 3: round_d(std::integral_constant<int, 3>{}); break;
+                    case 4: round_d(std::integral_constant<int, 4>{}); break;
+                    case 5: round_d(std::integral_constant<int, 5>{}); break;
+                    case 6: round_d(std::integral_constant<int, 6>{}); break;
+                    case 7: round_d(std::integral_constant<int, 7>{}); break;
+                    default: round_d(std::integral_constant<int, JCAP / 32>{}); break;
                     }
-                };
-                // warp-uniform: half-width rounds when the i's candidates fit
-                if (nj - skip_to <= 32 * (NTEST / 2)) {
-                    round(std::integral_constant<int, NTEST / 2>{}, skip_to);
-                } else {
-                    for (int kb = skip_to; kb < nj; kb += 32 * NTEST) round(std::integral_constant<int, NTEST>{}, kb);
+                    if (lane == 0) op.count_examined((nj - skip_a) + (has_b ? nj - skip_b : 0));
                 }
-                if (lane == 0) op.count_examined(nj - skip_to - (self_k >= 0 ? 1 : 0));
+            } else {
+                for (int il = ig; il < ig + ni; il++) {
+                    const int si = s0 + il;
+                    const bool in_seg = self_n > 0 && il >= self_lo && il < self_lo + self_n;
+                    const float4 ci = in_seg ? T.cand(self_base + il - self_lo) : com[si];
+                    const int skip_to = (self_n > 0 && HALF) ? max(0, min(self_n, il - self_lo + 1)) : 0;
+                    const int self_k = (!HALF && in_seg) ? self_base + (il - self_lo) : -1;
+                    const int tag = (il - ig) << 16;
+                    // squared COM distance of candidate k (huge if k is not a candidate of i)
+                    auto dist2 = [&](int k) -> float {
+                        if (k >= nj || (!HALF && k == self_k)) return 3.0e38f;
+                        const float4 cj = T.cand(k);
+                        const float X0 = ci.x - cj.x, X1 = ci.y - cj.y, X2 = ci.z - cj.z;
+                        return X0 * X0 + X1 * X1 + X2 * X2;
+                    };
+                    // the same test in FP64 from the FP64 state (pairs near the cut-off)
+                    auto test64 = [&](int k) -> bool {
+                        int dx, dy, dz, kx, ky, kz;
+                        stencil_offset<M>(HALF, T.jst[k], dx, dy, dz);
+                        wrap_axis(cx, dx, g.nc[0], kx);
+                        wrap_axis(cy, dy, g.nc[1], ky);
+                        wrap_axis(cz, dz, g.nc[2], kz);
+                        const double *ri = r64 + 3LL * si, *rj = r64 + 3LL * T.cand_slot(k);
+                        const double e0 = __dsub_rn(__dsub_rn(ri[0], rj[0]), (double)kx * g.L[0]);
+                        const double e1 = __dsub_rn(__dsub_rn(ri[1], rj[1]), (double)ky * g.L[1]);
+                        const double e2 = __dsub_rn(__dsub_rn(ri[2], rj[2]), (double)kz * g.L[2]);
+                        return __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2)) < g.rc2;
+                    };
+                    // one test round: NT candidates per lane (independent tests),
+                    // then the hits are appended in candidate order
+                    auto round = [&](auto ntc, int kb) {
+                        constexpr int NT = decltype(ntc)::value;
+                        bool h[NT], near[NT], any_near = false;
+    #pragma unroll
+                        for (int u = 0; u < NT; u++) {
+                            const float d2 = dist2(kb + 32 * u + lane);
+                            h[u] = d2 < g.rc2f;
+                            near[u] = fabsf(d2 - g.rc2f) < g.bandf;
+                            any_near |= near[u];
+                        }
+                        if (__any_sync(FULLMASK, any_near)) {  // rare: decide in FP64
+    #pragma unroll
+                            for (int u = 0; u < NT; u++)
+                                if (near[u]) h[u] = test64(kb + 32 * u + lane);
+                        }
+    #pragma unroll
+                        for (int u = 0; u < NT; u++) {
+                            const unsigned bal = __ballot_sync(FULLMASK, h[u]);
+                            if (h[u]) T.queue[qn + __popc(bal & lt_mask)] = tag | (kb + 32 * u + lane);
+                            qn += __popc(bal);
+                        }
+                        if constexpr (!Op::RUNS) {
+                            while (qn >= 32) {
+                                __syncwarp();
+                                chunk(32);
+                                __syncwarp();
+                                for (int t = lane; t < qn - 32; t += 32) T.queue[t] = T.queue[32 + t];
+                                qn -= 32;
+                                __syncwarp();
+                            }
+                        }
+                    };
+                    // run-drained: keep room for one more full test round
+                    auto make_room = [&]() {
+                        if constexpr (Op::RUNS) {
+                            if (qn > Tile::QCAPACITY - 32 * NTEST) {
+                                __syncwarp();
+                                op.drain(T, qn, s0 + ig, lane, exact_in, g.rc2f - g.bandf);
+                                qn = 0;
+                                __syncwarp();
+                            }
+                        }
+                    };
+                    {
+                        // warp-uniform: half-width rounds when the i's candidates fit
+                        if (nj - skip_to <= 32 * (NTEST / 2)) {
+                            make_room();
+                            round(std::integral_constant<int, NTEST / 2>{}, skip_to);
+                        } else {
+                            for (int kb = skip_to; kb < nj; kb += 32 * NTEST) {
+                                make_room();
+                                round(std::integral_constant<int, NTEST>{}, kb);
+                            }
+                        }
+                    }
+                    if (lane == 0) op.count_examined(nj - skip_to - (self_k >= 0 ? 1 : 0));
+                }
             }
             if (qn > 0) {
                 __syncwarp();
-                chunk(qn);
+                if constexpr (Op::RUNS) op.drain(T, qn, s0 + ig, lane, exact_in, g.rc2f - g.bandf);
+                else chunk(qn);
             }
             __syncwarp();
             op.seg_end(T, nj, lane);
