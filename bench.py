@@ -188,30 +188,87 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(seconds_budget=20.0):
-    """The oracle as it stands, timed on this host's cores on a bounded
-    sample of the bench workload (full-size force evaluations)."""
+def rel_err(A, B):
+    """Floored relative error per molecule, |A_i - B_i| / max(|B_i|, 0.01 rms|B|)."""
+    rms = math.sqrt(float((B ** 2).sum(axis=1).mean())) if len(B) else 1.0
+    return np.linalg.norm(A - B, axis=1) / np.maximum(np.linalg.norm(B, axis=1), max(0.01 * rms, 1e-300))
+
+
+def cpu_leg(cfg, gpu, md, torch, dev, seconds_budget=20.0, drift=True):
+    """The oracle legs of the default run (rank 0 at N = 1 only):
+    cpu_baseline: the FP64 oracle as it stands, timed on this host's cores on
+      a bounded sample of the bench workload (full-size force evaluations of
+      the bench's start state);
+    accuracy: the GPU path against the first of those oracle evaluations
+      (gpu = forces, torques and observables of the same state from a fresh
+      system): floored relative force and torque errors, energy and virial
+      errors relative to sum |u_ij|, sum |w_ij|, exact pair counts; and the
+      NVE energy drift per step per molecule, GPU and oracle, over 1000 steps
+      of a 4000-molecule 2CLJQ fluid after the oracle's thermostatted
+      warm-up (200 steps at dt / 10, 100 at dt)."""
     import oracle
-    cfg = mdgen.config_2cljq()
     s = oracle.setup_from_config(cfg)
     t0 = time.perf_counter()
     n = 0
     pairs = 0.0
+    first = None
     while True:
-        _, _, o = oracle.forces(cfg["model"], s, cfg["r"], cfg["q"], use_cells=True)
+        Fo, to, o = oracle.forces(cfg["model"], s, cfg["r"], cfg["q"], use_cells=True)
+        first = first or (Fo, to, o)
         n += 1
         pairs += o["n_site_pairs"]
         if time.perf_counter() - t0 > seconds_budget / 2 or n >= 8:
             break
-    dt = time.perf_counter() - t0
-    # the same evaluation on one thread (one full-size evaluation)
+    dt_all = time.perf_counter() - t0
     t1 = time.perf_counter()
     _, _, o1 = oracle.forces(cfg["model"], s, cfg["r"], cfg["q"], use_cells=True, n_threads=1)
     dt1 = time.perf_counter() - t1
-    return {"value": pairs / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} full-size oracle force evaluations (linked cells, N=262144, all host cores)",
-            "one_thread": {"value": o1["n_site_pairs"] / dt1, "unit": UNIT, "cores": 1,
-                           "sample": "1 full-size oracle force evaluation on one thread"}}
+    cpu = {"value": pairs / dt_all, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{n} full-size oracle force evaluations (linked cells, N={cfg['r'].shape[0]}, all host cores)",
+           "one_thread": {"value": o1["n_site_pairs"] / dt1, "unit": UNIT, "cores": 1,
+                          "sample": "1 full-size oracle force evaluation on one thread"}}
+    Fo, to, o = first
+    ef, et = rel_err(gpu["F"], Fo), rel_err(gpu["tau"], to)
+    obs = gpu["obs"]
+    acc = {"reference": "FP64 oracle, same state (bench start), every molecule",
+           "force_rel_median": float(np.median(ef)), "force_rel_max": float(ef.max()),
+           "torque_rel_median": float(np.median(et)), "torque_rel_max": float(et.max()),
+           "energy_rel_sum_abs": abs(obs["U_pot"] - o["U"]) / o["abs_U"],
+           "virial_rel_sum_abs": abs(obs["W"] - o["W"]) / o["abs_W"],
+           "pairs_exact": obs["n_mol_pairs"] == int(o["n_mol_pairs"]),
+           "U_per_molecule": o["U"] / cfg["r"].shape[0]}
+    if drift:
+        acc["nve_drift"] = drift_leg(md, oracle)
+    return cpu, acc
+
+
+def drift_leg(md, oracle, n=4000, n_steps=1000, every=10):
+    cfg = mdgen.config_2cljq(n=n)
+    setup = oracle.setup_from_config(cfg)
+    st = {k: cfg[k] for k in ("r", "v", "q", "j")}
+    st = oracle.step(cfg["model"], setup, st, cfg["dt"] / 10, 200, use_cells=True, T_target=cfg["T"])
+    st = oracle.step(cfg["model"], setup, st, cfg["dt"], 100, use_cells=True, T_target=cfg["T"])
+    start = {k: st[k] for k in ("r", "v", "q", "j")}
+    dt, m = cfg["dt"], n_steps // every
+    g = md.System(cfg, deterministic=1)
+    g.set(start["r"], start["q"], start["v"], start["j"])
+    Eg, Eo = [], []
+    for _ in range(m):
+        g.step(every, dt)
+        ob = g.observables()
+        Eg.append(ob["U_pot"] + ob["K_trans"] + ob["K_rot"])
+    g.close()
+    st = dict(start)
+    for _ in range(m):
+        st = oracle.step(cfg["model"], setup, st, dt, every, use_cells=True)
+        kt, kr = oracle.kinetic(cfg["model"], dt, st["v"], st["q"], st["j"], st["F"], st["tau"])
+        Eo.append(st["obs"]["U"] + kt + kr)
+    t = np.arange(1, m + 1) * every
+    fg, fo = np.polyfit(t, np.array(Eg), 1), np.polyfit(t, np.array(Eo), 1)
+    return {"system": f"2CLJQ N={n} rho=0.55 dt={dt}, NVE after oracle warm-up", "steps": n_steps,
+            "gpu_per_step_per_molecule": float(fg[0] / n), "oracle_per_step_per_molecule": float(fo[0] / n),
+            "oracle_fluctuation_rms_per_molecule": float(np.std(np.array(Eo) - np.polyval(fo, t)) / n),
+            "E_per_molecule": float(Eo[0] / n), "gpu_shell": "full (deterministic)"}
 
 
 def main():
@@ -225,6 +282,9 @@ def main():
                     help="cells per cut-off length: 1 (27-cell stencil) or 2 (125-cell stencil, §3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-drift", action="store_true", help="default run: skip the 1000-step NVE drift leg")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="default run: skip the compact secondary workloads (LJ N=4096, slab, replicas, adjoint)")
     ap.add_argument("--workload", default="2cljq",
                     choices=["2cljq", "batch", "adjoint", "lj", "slab", "lj200m", "sweep"],
                     help="2cljq: the headline step; batch: 512 uneven replicas; adjoint: parameter gradients; "
@@ -232,7 +292,7 @@ def main():
                          "lj200m: homogeneous LJTS N=200M, one force evaluation; "
                          "sweep: LJTS fluid time per molecule-step for N = 4096 ... 16.8M")
     ap.add_argument("--replicas", type=int, default=512)
-    ap.add_argument("--configs", type=int, default=4, help="adjoint workload: configurations per ensemble")
+    ap.add_argument("--configs", type=int, default=64, help="adjoint workload: configurations per ensemble")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -248,14 +308,13 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    if args.workload == "batch":
-        return run_batch(args, md, torch, dev, rank)
-    if args.workload == "adjoint":
-        return run_adjoint(args, md, torch, dev, rank)
-    if args.workload in ("lj", "slab", "lj200m"):
-        return run_single(args, md, torch, dev, rank)
-    if args.workload == "sweep":
-        return run_sweep(args, md, torch, dev, rank)
+    other = {"batch": run_batch, "adjoint": run_adjoint, "lj": run_single, "slab": run_single,
+             "lj200m": run_single, "sweep": run_sweep}
+    if args.workload in other:
+        line = other[args.workload](args, md, torch, dev, rank)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     cfg = mdgen.config_2cljq(seed_k=rank)
     half = args.shell == "half"
     sysm = md.System(cfg, deterministic=0 if half else 1, half_shell=1 if half else 0, cell_div=args.cell_div)
@@ -310,18 +369,39 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    # the measured FP32 peak: FMA chains at full occupancy (md_fp32_peak),
+    # scalar and paired f32x2 instructions
+    pk_scalar, _ = md.md_fp32_peak(False)
+    pk_paired, _ = md.md_fp32_peak(True)
+    pk_meas = max(pk_scalar, pk_paired) / 1e12
+    traffic = force_traffic() if half else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": force_traffic() if half else None,
+            "traffic": traffic,
+            "traffic_source": ("dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the committed "
+                               "ncu summary profiles/k_force_2cljq_N262144.md (its recorded source hash matches "
+                               "the force kernel's sources)") if traffic is not None else
+                              "null: no ncu capture of the force kernel as its sources are now",
             "kernel": "k_force (2CLJQ, " + ("half" if half else "full") + " shell)",
-            "flops_per_pair": fpp, "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
-            f"{sm_max:.0f} MHz (FP32 FMA)",
+            "flops_per_pair": fpp,
+            "flops_basis": "FP32 operations of the method per unordered interacting molecule pair "
+                           "(include/md_flops.h; FMA = 2; per-molecule geometry formed again per pair not counted)",
+            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (FP32 FMA, "
+                          "unit-count formula)",
+            "peak_measured": pk_meas, "frac_of_measured": achieved / pk_meas,
+            "peak_measured_basis": f"md_fp32_peak: FMA-chain kernel, scalar {pk_scalar / 1e12:.2f}, paired f32x2 "
+                                   f"{pk_paired / 1e12:.2f} TFLOP/s (of measured)",
             "frac_at_sampled_clock": (achieved / (peak * clk["sm_mhz"] / sm_max)) if clk.get("sm_mhz") else None,
             "force_ms_per_launch": f_ms}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 site math, f64 accumulation/state",
-            "data": "synthetic (seeded 2CLJQ fluid, random orientations)",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("f32 site math; per-molecule force/torque in f32 (half shell: per-lane run sums and f32 "
+                      "vector reductions into per-molecule records); energy/virial f32 pass sums into f64; "
+                      "f64 state and integrator") if half else
+                     ("f32 site math; per-molecule force/torque: f32 warp sums of <= 32 pair terms into f64; "
+                      "energy/virial f32 pass sums into f64; f64 state and integrator"),
+            "data": "synthetic (seeded 2CLJQ fluid, random orientations with close site contacts relieved)",
             "config": {"workload": WORKLOAD_2CLJQ,
                        "shell": args.shell, "cells_per_cutoff": args.cell_div,
                        "l2": "flushed (512 MB write) before every timed step",
@@ -332,15 +412,73 @@ def main():
             "gpu_launches": KERNELS_PER_STEP * args.steps,
             "roofline": roof, "clocks": clk}
 
+    sysm.close()
     if not args.no_e2e:
         line["e2e"] = e2e_run(args, cfg, md, torch, dev)
-    if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the GPU path's forces of the bench's start state, for the accuracy leg
+        g = md.System(cfg, deterministic=0 if half else 1, half_shell=1 if half else 0, cell_div=args.cell_div)
+        g.set(t["r"], t["q"], t["v"], t["j"])
+        g.compute_forces()
+        F, tau = g.forces()
+        gpu = {"F": F, "tau": tau, "obs": g.observables()}
+        g.close()
+        line["cpu_baseline"], line["accuracy"] = cpu_leg(cfg, gpu, md, torch, dev, drift=not args.no_drift)
+    if rank == 0 and world == 1 and not args.no_secondary:
+        line["secondary"] = secondary(args, md, torch, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    sysm.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def secondary(args, md, torch, dev):
+    """Compact runs of the other workloads, recorded in the default line
+    beside the headline (each its own seeded input, CUDA-event timing):
+    the LJTS fluid N = 4096 (md_step, single calls and graph replay), the
+    LJTS vapour-liquid slab N = 4,194,304, the 512 batched replicas against
+    the same replicas as separate systems, and the adjoint (parameter
+    gradients) against the forward force kernel on the same 4-site
+    configurations.  A failure in one is recorded in place of its numbers."""
+    import copy
+    out = {}
+
+    def sub(workload, **kw):
+        a = copy.copy(args)
+        a.workload, a.warmup, a.cell_div = workload, 3, 1
+        for k, v in kw.items():
+            setattr(a, k, v)
+        t0 = time.perf_counter()
+        fn = {"batch": run_batch, "adjoint": run_adjoint, "lj": run_single, "slab": run_single}[workload]
+        line = fn(a, md, torch, dev, 0)
+        line["wall_s"] = time.perf_counter() - t0
+        return line
+
+    def keep(line, keys):
+        return {k: line[k] for k in keys if k in line}
+
+    for name, workload, kw, keys in (
+            ("lj_fluid_4096", "lj", {"steps": 20}, ("value", "ms_per_step", "graph_replay", "force_ms_per_launch",
+                                                    "molecule_updates_per_s", "mol_pairs_per_eval", "wall_s")),
+            ("lj_slab_4194304", "slab", {"steps": 5}, ("value", "ms_per_step", "force_ms_per_launch",
+                                                       "molecule_updates_per_s", "mol_pairs_per_eval", "wall_s")),
+            ("replicas_512", "batch", {"steps": 10, "replicas": 512},
+             ("value", "ms_per_step", "molecule_updates_per_s", "sequential", "speedup_vs_sequential", "tuned",
+              "wall_s")),
+            ("adjoint_4site_50000", "adjoint", {"steps": 4, "configs": 2},
+             ("adjoint_kernel_ms_per_config", "forward_force_kernel_ms_per_config", "adjoint_ms_per_ensemble",
+              "forward_ms_per_ensemble", "config", "wall_s"))):
+        try:
+            line = sub(workload, **kw)
+            d = keep(line, keys)
+            d["unit"] = line.get("unit")
+            if "roofline" in line:
+                d["frac"] = line["roofline"]["frac"]
+            out[name] = d
+        except Exception as e:  # recorded, the headline line still prints
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
+    return out
 
 
 def e2e_run(args, cfg, md, torch, dev):
@@ -445,8 +583,7 @@ def run_single(args, md, torch, dev, rank):
             "clocks": clk}
     if graph is not None:
         line["graph_replay"] = graph
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def timed_calls(fn, steps, stream, torch, flush=None):
@@ -504,8 +641,7 @@ def run_sweep(args, md, torch, dev, rank):
                        "l2": "flushed (512 MB write) before every timed md_step(1); graph_replay_ms_per_step: one "
                              "md_step(steps) call, not flushed between its steps"},
             "sweep": rows}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_batch(args, md, torch, dev, rank):
@@ -579,8 +715,7 @@ def run_batch(args, md, torch, dev, rank):
                            "note": f"{len(cfgs)} separate md_system handles, md_step(1, T_target) each per step"},
             "speedup_vs_sequential": (t_seq / seq_steps) / (t_batch / args.steps),
             "tuned": tune, "clocks": clk}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_adjoint(args, md, torch, dev, rank):
@@ -588,7 +723,7 @@ def run_adjoint(args, md, torch, dev, rank):
     rho = 0.5, rc = 3): md_param_grad over an ensemble of configurations,
     beside the plain force kernel on the same configurations."""
     from paper_1408_4599_gb300.autograd import ensemble_uw
-    cfgs = [mdgen.config_4site(cfg=c) for c in range(args.configs)]
+    cfgs = mdgen.configs_4site(args.configs)  # cached; generated by a spawn pool when missing
     r_all = torch.from_numpy(np.stack([c["r"] for c in cfgs])).to(dev)
     q_all = torch.from_numpy(np.stack([c["q"] for c in cfgs])).to(dev)
     s = md.System(cfgs[0], deterministic=0, half_shell=1)
@@ -636,8 +771,7 @@ def run_adjoint(args, md, torch, dev, rank):
             "forward_ms_per_ensemble": 1e3 * t_fwd, "adjoint_ms_per_ensemble": 1e3 * t_adj,
             "dU": dU.tolist(), "dW": dW.tolist(), "U_mean": U, "W_mean": W,
             "autograd_grad": theta.grad.tolist()}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 if __name__ == "__main__":

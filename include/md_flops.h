@@ -15,11 +15,13 @@
  * test of an examined candidate (MD_FLOPS_EXAMINED) is overhead and is not
  * counted either (§3: only ~16% of the examined pairs interact).
  *
+ * The space-frame geometry of a molecule (site offsets R(q) d_a, axes
+ * R(q) e_a) is a per-molecule quantity of the method; a kernel that forms
+ * it again per pair (the linear-molecule path forms z_a u from the packed
+ * axis u) does so as overhead, not counted.
+ *
  * Building blocks (2CLJQ is compiled as a linear molecule with its
- * quadrupole at the centre of mass: the packed geometry is the molecular
- * axis u, site offsets are z_a u):
- *   site offsets z_a u of the 2 LJ sites of i and of j ............ 12
- *   quadrupole axes of i and j .................................... 6
+ * quadrupole at the centre of mass: site offsets are z_a u):
  *   lever arm X + z_a u, LJ sites of i ............................. 6
  *   LJ-LJ site pair: x = (X + z_a u_i) - z_b u_j 3, r^2 5, rcp 1,
  *     s^2 1, s^6 2, F/r 5, energy 5, site force 3, sum into a 3 .... 28  (1 MUFU)
@@ -43,8 +45,8 @@
 #define MD_MUFU_PAIR_LJ1 1
 
 /* 2CLJQ: 2 LJ sites + 1 linear quadrupole at the centre of mass:
- * 12 + 6 + 6 + 4 x 28 + 127 + 3 x 3 + 24 + 12 + 6 + 1 + 9 + 6 = 330 */
-#define MD_FLOPS_PAIR_2CLJQ 330
+ * 6 + 4 x 28 + 127 + 3 x 3 + 24 + 12 + 6 + 1 + 9 + 6 = 312 */
+#define MD_FLOPS_PAIR_2CLJQ 312
 #define MD_MUFU_PAIR_2CLJQ 5
 
 /* distance test of one examined candidate (overhead, not counted above) */

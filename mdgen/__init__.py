@@ -26,6 +26,8 @@ principal-axes frame (the generator guarantees it).  Quaternions are
 from __future__ import annotations
 
 import math
+import os
+
 import numpy as np
 
 SEED_BASE = 1408_0000
@@ -204,6 +206,54 @@ def resolve_site_overlaps(model: dict, r: np.ndarray, q: np.ndarray, box, rng: n
     return q
 
 
+def relieve_site_overlaps(model: dict, r: np.ndarray, q: np.ndarray, box, rng: np.random.Generator,
+                          d_min: float = 0.85, tries: int = 24, max_passes: int = 40) -> np.ndarray:
+    """Geometric relief of close contacts between molecules of a lattice
+    start with random orientations (positions stay).  Each pass finds the
+    molecules with an interaction site closer than d_min to a site of
+    another molecule, takes a random half of them, and gives each the
+    orientation, among its current one and `tries` random ones, whose
+    sites lie farthest from every other molecule's sites; until no contact
+    is left or max_passes is reached.  Purely geometric: no interaction
+    law is evaluated.  Returns the new quaternions."""
+    from scipy.spatial import cKDTree
+    box = np.asarray(box, float)
+    pts = np.unique(np.array([e["pos"] for key in ("lj", "charges", "dipoles", "quads") for e in model[key]], float),
+                    axis=0)
+    S, n = len(pts), r.shape[0]
+    q = q.copy()
+
+    def sites(rr, qq):
+        m = rr.shape[0]
+        off = _rotate_body_to_space(np.repeat(qq, S, axis=0), np.tile(pts, (m, 1))).reshape(m, S, 3)
+        return np.mod(rr[:, None, :] + off, box).reshape(-1, 3)
+
+    own = np.repeat(np.arange(n), S)
+
+    def nearest_other(tree, pos, mine):
+        # distance from each point to the nearest site of another molecule
+        # (among its S + 1 nearest sites: at most S are the molecule's own)
+        d, idx = tree.query(pos, k=S + 1, workers=-1)
+        return np.where(own[np.minimum(idx, n * S - 1)] == mine[:, None], np.inf, d).min(axis=1)
+
+    for _ in range(max_passes):
+        sp = sites(r, q)
+        tree = cKDTree(sp, boxsize=box)
+        close = nearest_other(tree, sp, own) < d_min
+        if not close.any():
+            break
+        bad = np.unique(own[close])
+        rng.shuffle(bad)
+        bad = bad[: max(1, len(bad) // 2)]
+        nb, K = len(bad), tries + 1
+        cand = np.concatenate([q[bad][:, None, :], random_quaternions(nb * tries, rng).reshape(nb, tries, 4)], axis=1)
+        d = nearest_other(tree, sites(np.repeat(r[bad], K, axis=0), cand.reshape(-1, 4)),
+                          np.repeat(np.repeat(bad, K), S))
+        best = d.reshape(nb, K, S).min(axis=2).argmax(axis=1)
+        q[bad] = cand[np.arange(nb), best]
+    return q
+
+
 def mb_velocities(n: int, T: float, mass: float, rng: np.random.Generator) -> np.ndarray:
     """Maxwell-Boltzmann velocities at temperature T, zero total momentum,
     rescaled so that sum(m v^2) = (3n - 3) T exactly."""
@@ -259,14 +309,22 @@ def config_lj_fluid(n: int = 4096, rho: float = 0.6, T: float = 0.95, rc: float 
             "lj_shift": 1, "lj_lrc": 0, "eps_rf": math.inf, "dt": 0.002, "T": T, **st}
 
 
-def config_2cljq(n: int = 262144, rho: float = 0.55, T: float = 1.0, rc: float = 3.0, seed_k: int = 0) -> dict:
-    """2CLJQ fluid (elongation 0.5, Q*^2 = 2): fcc subset, random orientations."""
+def config_2cljq(n: int = 262144, rho: float = 0.55, T: float = 1.0, rc: float = 3.0, seed_k: int = 0,
+                 relieve: bool = True) -> dict:
+    """2CLJQ fluid (elongation 0.5, Q*^2 = 2): fcc subset, random
+    orientations; with `relieve`, orientations giving intermolecular site
+    contacts closer than 0.85 sigma are replaced (relieve_site_overlaps), so
+    that the start is a fluid-like configuration (negative energy) rather
+    than one dominated by a few overlapping pairs."""
     rng = np.random.default_rng(seed_for(2, seed_k))
     L = (n / rho) ** (1.0 / 3.0)
     box = (L, L, L)
     model = model_2cljq()
     pos = fcc_subset(n, box, rng, jitter=0.05)
     st = _state(model, box, rng, T, pos)
+    if relieve:
+        st["q"] = relieve_site_overlaps(model, st["r"], st["q"], box, rng, d_min=0.85)
+        st["j"] = angular_momenta(st["q"], model_principal_moments(model), T, rng)
     return {"name": f"2cljq-N{n}", "model": model, "box": box, "rc": rc,
             "lj_shift": 0, "lj_lrc": 1, "eps_rf": math.inf, "dt": 0.001, "T": T, **st}
 
@@ -362,17 +420,17 @@ def config_replica(k: int, n: int, rho: float, T: float, rc: float = 3.0) -> dic
 
 def config_4site(n: int = 50000, rho: float = 0.5, T: float = 1.0, rc: float = 3.0, cfg: int = 0) -> dict:
     """One configuration of the 4-site polar model (force-field gradient
-    workload): fcc subset, random orientations (re-drawn where sites of
-    different molecules overlap), seeded per configuration."""
+    workload): fcc subset, random orientations (close intermolecular site
+    contacts relieved, relieve_site_overlaps), seeded per configuration."""
     rng = np.random.default_rng(seed_for(5, cfg))
     L = (n / rho) ** (1.0 / 3.0)
     box = (L, L, L)
     model = model_4site()
     pos = fcc_subset(n, box, rng, jitter=0.05)
     st = _state(model, box, rng, T, pos)
-    # lattice start with random orientations: re-draw overlapping ones so that
-    # no two sites of different molecules are closer than 0.6 sigma
-    st["q"] = resolve_site_overlaps(model, st["r"], st["q"], box, rng, d_min=0.6)
+    # lattice start with random orientations: relieve the close site
+    # contacts between molecules (0.8 sigma)
+    st["q"] = relieve_site_overlaps(model, st["r"], st["q"], box, rng, d_min=0.8)
     st["j"] = angular_momenta(st["q"], model_principal_moments(model), T, rng)
     return {"name": f"4site-N{n}-cfg{cfg}", "model": model, "box": box, "rc": rc,
             "lj_shift": 0, "lj_lrc": 1, "eps_rf": math.inf, "dt": 0.001, "T": T, **st}
@@ -402,3 +460,56 @@ def random_cluster(model: dict, n: int, box, rng: np.random.Generator, min_sep: 
             pts.append(p)
     pos = np.array(pts)
     return _state(model, box, rng, 1.0, pos)
+
+
+# --------------------------------------------------------------------------
+# Cached ensembles (the overlap relief of the 4-site lattice starts takes
+# seconds per configuration; generated configurations are kept on disk)
+# --------------------------------------------------------------------------
+
+_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_cache")
+
+
+def _source_tag() -> str:
+    import hashlib
+    with open(os.path.abspath(__file__), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:12]
+
+
+def _config_4site_cached(args):
+    n, rho, T, rc, c = args
+    path = os.path.join(_CACHE, f"4site_n{n}_rho{rho}_T{T}_rc{rc}_cfg{c}_{_source_tag()}.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        st = {k: z[k] for k in ("r", "v", "q", "j")}
+    else:
+        cfg = config_4site(n=n, rho=rho, T=T, rc=rc, cfg=c)
+        st = {k: cfg[k] for k in ("r", "v", "q", "j")}
+        os.makedirs(_CACHE, exist_ok=True)
+        tmp = path + f".{os.getpid()}.tmp.npz"
+        np.savez(tmp, **st)
+        os.replace(tmp, path)
+    return st
+
+
+def configs_4site(n_cfg: int, n: int = 50000, rho: float = 0.5, T: float = 1.0, rc: float = 3.0,
+                  workers: int = 0) -> list:
+    """Configurations 0 .. n_cfg-1 of config_4site, generated in parallel
+    (a 'spawn' process pool: safe after the caller has initialised CUDA) and
+    kept in mdgen/_cache/ keyed by the arguments and this file's contents."""
+    import multiprocessing as mp
+    jobs = [(n, rho, T, rc, c) for c in range(n_cfg)]
+    workers = workers or min(len(jobs), os.cpu_count() or 1)
+    if workers > 1 and len(jobs) > 1:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            states = pool.map(_config_4site_cached, jobs)
+    else:
+        states = [_config_4site_cached(j) for j in jobs]
+    base = config_4site(n=8, rho=rho, T=T, rc=rc)  # model and settings only
+    out = []
+    for c, st in enumerate(states):
+        cfg = {k: v for k, v in base.items() if k not in ("r", "v", "q", "j")}
+        L = (n / rho) ** (1.0 / 3.0)
+        cfg.update(st, box=(L, L, L), name=f"4site-N{n}-cfg{c}")
+        out.append(cfg)
+    return out

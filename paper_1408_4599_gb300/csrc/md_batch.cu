@@ -59,7 +59,7 @@ struct md_batch {
     int *work = nullptr;  // [half list | full list] of cells, longest replicas first
     long long n_work_half = 0, n_work_full = 0;
     int *counters = nullptr;  // work-queue heads (2)
-    float *cellE = nullptr;   // 5 per cell
+    double *cellE = nullptr;  // 5 per cell
     int *cellN = nullptr;     // 2 per cell
     double *rep_obs = nullptr;  // 8 per replica
     double *rep_kin = nullptr;  // 2 per replica
@@ -185,7 +185,7 @@ struct BatchArgs {
     long long n_work;
     int *counter;
     int chunk;
-    float *cellE;
+    double *cellE;
     int *cellN;
 };
 
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(MD_WARPS * 32) k_force_batch(const __grid_cons
             gv.bandf = B.f.g.bandf;
             gv.cell0 = rg.cell0;
             traverse_cell<SIG, HALF>(m, gv, B.f.cell_start, B.f.com, B.f.geo, B.f.r, K, c - rg.cell0, *T, op, lane);
-            float v[5];
+            double v[5];
             int nm, ne;
             op_warp_totals(op, v, nm, ne);
             if (lane == 0) {
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(MD_WARPS * 32) k_force_batch(const __grid_cons
 }
 
 // One block per replica: energies/virials/counts (fixed summation order).
-__global__ void k_rep_reduce(const RepGrid *G, int n_sys, long long ncell, const float *cellE, const int *cellN,
+__global__ void k_rep_reduce(const RepGrid *G, int n_sys, long long ncell, const double *cellE, const int *cellN,
                              int site_pairs, double *out)
 {
     const int k = blockIdx.x;
@@ -243,7 +243,7 @@ __global__ void k_rep_reduce(const RepGrid *G, int n_sys, long long ncell, const
     __shared__ double sh[8][32];
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-        for (int q = 0; q < 5; q++) acc[q] += (double)cellE[5 * c + q];
+        for (int q = 0; q < 5; q++) acc[q] += cellE[5 * c + q];
         acc[5] += (double)cellN[2 * c];
         acc[7] += (double)cellN[2 * c + 1];
     }
@@ -582,14 +582,14 @@ md_status md_batch_create(int32_t n_sys, const double *boxes, double cutoff, con
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->rep_of_cell, sizeof(int) * nc_tot);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->work, sizeof(int) * nc_tot);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->counters, sizeof(int) * 2);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b->cellE, sizeof(float) * 5 * nc_tot);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->cellE, sizeof(double) * 5 * nc_tot);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->cellN, sizeof(int) * 2 * nc_tot);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->rep_obs, sizeof(double) * 8 * n_sys);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->rep_kin, sizeof(double) * 2 * n_sys);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->rep_T, sizeof(double) * n_sys);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->rep_beta, sizeof(double) * n_sys);
     if (e == cudaSuccess) e = cudaMemset(b->rep_T, 0, sizeof(double) * n_sys);
-    if (e == cudaSuccess) e = cudaMemset(b->cellE, 0, sizeof(float) * 5 * nc_tot);
+    if (e == cudaSuccess) e = cudaMemset(b->cellE, 0, sizeof(double) * 5 * nc_tot);
     if (e == cudaSuccess) e = cudaMemset(b->cellN, 0, sizeof(int) * 2 * nc_tot);
     if (e == cudaSuccess) {
         std::vector<int> roc(nc_tot);

@@ -87,13 +87,12 @@ __global__ void __launch_bounds__(MD_WARPS * 32, force_min_blocks<SIG, HALF>()) 
         });
     }
 
-    // block partials: FP32 warp sums of the compensated lane sums; FP64 only
-    // once per value per block
-    float v[5] = {op.total(0), op.total(1), op.total(2), op.total(3), op.total(4)};
+    // block partials: FP64 warp sums of the lanes' FP64 totals
+    double v[5] = {op.total(0), op.total(1), op.total(2), op.total(3), op.total(4)};
     for (int q = 0; q < 5; q++)
         for (int msk = 16; msk > 0; msk >>= 1) v[q] += __shfl_xor_sync(FULLMASK, v[q], msk);
     const int wm = __reduce_add_sync(FULLMASK, op.nmol), we = __reduce_add_sync(FULLMASK, op.nexam);
-    __shared__ float s_red[MD_WARPS][5];
+    __shared__ double s_red[MD_WARPS][5];
     __shared__ long long s_cnt[MD_WARPS][2];
     if (lane == 0) {
         for (int q = 0; q < 5; q++) s_red[warp][q] = v[q];

@@ -32,12 +32,11 @@ template <class SIG, int M>
 cudaError_t launch_force_sig(const ForceArgs &A, int half_shell, int n_blocks, cudaStream_t s);
 
 struct ForceExtraHalf {
-    float tot[10][32];  // per lane: compensated totals (sum, compensation) of U, W, W_xx, W_yy, W_zz
+    double tot[5][32];  // per lane: FP64 totals of U, W, W_xx, W_yy, W_zz (FP32 pass sums added once per pass)
 };
 struct ForceExtra {
-    float4 if4[32];     // i totals of the pass (full shell): F, tau_x
-    float2 it2[32];     // tau_y, tau_z
-    float tot[10][32];
+    double it[6][32];   // full shell: FP64 totals of F and tau of the pass's i molecules (FP32 chunk sums added)
+    double tot[5][32];
 };
 
 template <class SIG, bool HALF>
@@ -70,19 +69,18 @@ struct ForceOp {
     __device__ void reset_totals()
     {
 #pragma unroll
-        for (int q = 0; q < 10; q++) T->x.tot[q][ln] = 0.f;
+        for (int q = 0; q < 5; q++) T->x.tot[q][ln] = 0.0;
         nmol = nexam = 0;
     }
     // the lane's total of value q (0 U, 1 W, 2 W_xx, 3 W_yy, 4 W_zz)
-    __device__ float total(int q) const { return T->x.tot[2 * q][ln] - T->x.tot[2 * q + 1][ln]; }
+    __device__ double total(int q) const { return T->x.tot[q][ln]; }
     __device__ void pass_begin(int ig_, int ni, int lane)
     {
         ig = ig_;
         if constexpr (!HALF) {  // the half shell sums its i terms while draining
-            for (int t = lane; t < ni; t += 32) {
-                T->x.if4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-                T->x.it2[t] = make_float2(0.f, 0.f);
-            }
+            for (int t = lane; t < ni; t += 32)
+#pragma unroll
+                for (int q = 0; q < 6; q++) T->x.it[q][t] = 0.0;
         }
         cU = cW = cX = cY = cZ = 0.f;
     }
@@ -136,19 +134,9 @@ struct ForceOp {
                 if (take) v[q] += o;
             }
         }
-        if (head) {
-            float4 a = T->x.if4[il];
-            a.x += v[0];
-            a.y += v[1];
-            a.z += v[2];
-            if (NQ == 6) {
-                a.w += v[3];
-                float2 b = T->x.it2[il];
-                b.x += v[4];
-                b.y += v[5];
-                T->x.it2[il] = b;
-            }
-            T->x.if4[il] = a;
+        if (head) {  // the segment's FP32 sum (<= 32 pair terms) joins the i's FP64 total
+#pragma unroll
+            for (int q = 0; q < NQ; q++) T->x.it[q][il] += (double)v[q];
         }
         }
     }
@@ -233,16 +221,16 @@ struct ForceOp {
         if constexpr (!HALF) {
             for (int t = lane; t < ni; t += 32) {
                 const int si = s0 + ig_ + t;
-                const float4 i4 = T->x.if4[t];
-                const float2 i2 = T->x.it2[t];
-                const float ip[6] = {i4.x, i4.y, i4.z, i4.w, i2.x, i2.y};
+                double ip[6];
+#pragma unroll
+                for (int q = 0; q < 6; q++) ip[q] = T->x.it[q][t];
                 if (A.to_acc) {
                     float *a = A.acc + (long long)FACC_STRIDE * si;
-                    red_add_v4(a, ip[0], ip[1], ip[2], 0.f);
-                    if (NQ == 6) red_add_v4(a + 4, ip[3], ip[4], ip[5], 0.f);
+                    red_add_v4(a, (float)ip[0], (float)ip[1], (float)ip[2], 0.f);
+                    if (NQ == 6) red_add_v4(a + 4, (float)ip[3], (float)ip[4], (float)ip[5], 0.f);
                 } else {
                     double *Fo = A.F + 3LL * si, *To = A.tau + 3LL * si;
-                    const float t0 = NQ == 6 ? ip[3] : 0.f, t1 = NQ == 6 ? ip[4] : 0.f, t2 = NQ == 6 ? ip[5] : 0.f;
+                    const double t0 = NQ == 6 ? ip[3] : 0.0, t1 = NQ == 6 ? ip[4] : 0.0, t2 = NQ == 6 ? ip[5] : 0.0;
                     Fo[0] = ip[0];
                     Fo[1] = ip[1];
                     Fo[2] = ip[2];
@@ -255,14 +243,10 @@ struct ForceOp {
                 }
             }
         }
+        // the pass's FP32 lane sums join the lane's FP64 totals
         const float c5[5] = {cU, cW, cX, cY, cZ};
 #pragma unroll
-        for (int q = 0; q < 5; q++) {
-            float sq = T->x.tot[2 * q][ln], kq = T->x.tot[2 * q + 1][ln];
-            kahan_add(sq, kq, c5[q]);
-            T->x.tot[2 * q][ln] = sq;
-            T->x.tot[2 * q + 1][ln] = kq;
-        }
+        for (int q = 0; q < 5; q++) T->x.tot[q][ln] += (double)c5[q];
     }
 };
 
@@ -270,7 +254,7 @@ struct ForceOp {
 // Warp totals of the energy / virial sums and pair counts of one op (all
 // lanes return the same values).
 template <class Op>
-__device__ __forceinline__ void op_warp_totals(Op &op, float (&v)[5], int &nm, int &ne)
+__device__ __forceinline__ void op_warp_totals(Op &op, double (&v)[5], int &nm, int &ne)
 {
 #pragma unroll
     for (int q = 0; q < 5; q++) v[q] = op.total(q);

@@ -568,13 +568,6 @@ __device__ __forceinline__ void mol_pair(const DevModel &m, const float X0, cons
     Uo = U;
 }
 
-__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
-{
-    const float y = x - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-}
 
 // ------------------------------------------------------------- traversal
 #ifndef MD_JCAP

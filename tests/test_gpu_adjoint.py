@@ -28,8 +28,8 @@ LOG = os.environ.get("MD_PARITY_LOG")
 
 
 def _ensemble(name):
-    if name == "4site-50000":  # the full-size configuration, two of its configurations
-        cfgs = [mdgen.config_4site(cfg=c) for c in range(2)]
+    if name == "4site-50000":  # the full-size configuration, four of its configurations
+        cfgs = mdgen.configs_4site(4)
     elif name == "4site":
         cfgs = [mdgen.config_4site(n=3000, cfg=c) for c in range(3)]
     elif name == "2cljdq-rf":
@@ -67,6 +67,12 @@ def test_param_grad_matches_oracle(name):
     assert abs(U - Uo) <= 1e-5 * absU
     assert np.all(_close(dU, dUo, aU)), (dU, dUo, aU)
     assert np.all(_close(dW, dWo, aW)), (dW, dWo, aW)
+    # components that do not cancel heavily (|component| >= 1% of the sum of
+    # its terms' magnitudes) also meet a plain relative bound
+    for d, do, a in ((dU, dUo, aU), (dW, dWo, aW)):
+        big = np.abs(do) >= 1e-2 * a
+        rel = np.abs(d - do) / np.maximum(np.abs(do), 1e-300)
+        assert np.all(rel[big] <= 1e-4), (rel, big)
 
 
 def test_device_configurations_and_parameter_round_trip():

@@ -55,7 +55,15 @@ def test_batch_forces_match_oracle_per_replica(half):
 
 def test_batch_equals_single_systems():
     """Full stencil everywhere: the batched kernels and the single-system
-    kernels do the same arithmetic in the same order per molecule."""
+    kernels do the same arithmetic in the same order per molecule, except
+    that the batch keeps each molecule's FP64 force and torque totals in its
+    FP32 records (read by the batched integrator of mixed-shell replicas),
+    where the single system keeps them in FP64.  That rounding (2^-24 of a
+    molecule's total; forces reach ~1e4 in these overlapping lattice starts)
+    bounds the velocity difference after six steps by ~6 dt 2^-24 F_max / m
+    (a few roundings: 1e-6 relative is allowed), the positions by dt times
+    that; any difference in the arithmetic itself would show at the level of
+    the forces."""
     cfgs = _replicas(n_rep=6, seed_k=5)
     b = md.Batch(cfgs, half_shell=0).set()
     b.step(6, 0.001, use_graph=False)
@@ -68,16 +76,18 @@ def test_batch_equals_single_systems():
         s.step(6, 0.001)
         r1, v1, q1, j1 = s.molecules()
         o1 = s.observables()
+        F1, _ = s.forces()
         s.close()
         L = np.array(c["box"])
         dr = r - r1
         dr -= L * np.rint(dr / L)
-        assert np.abs(dr).max() < 1e-11 and np.abs(v - v1).max() < 1e-9
-        assert np.abs(q - q1).max() < 1e-11
+        dv_tol = 1e-6 * 6 * 0.001 * np.abs(F1).max() / mdgen.model_mass(c["model"])
+        assert np.abs(v - v1).max() < dv_tol and np.abs(dr).max() < 6 * 0.001 * dv_tol
+        assert np.abs(q - q1).max() < 1e-7
         assert o_b["n_mol_pairs"] == o1["n_mol_pairs"]
-        assert o_b["U_pot"] == pytest.approx(o1["U_pot"], rel=1e-9, abs=1e-9)
-        assert o_b["K_trans"] == pytest.approx(o1["K_trans"], rel=1e-12)
-        assert o_b["K_rot"] == pytest.approx(o1["K_rot"], rel=1e-12)
+        assert o_b["U_pot"] == pytest.approx(o1["U_pot"], rel=1e-6, abs=1e-9)
+        assert o_b["K_trans"] == pytest.approx(o1["K_trans"], rel=1e-6)
+        assert o_b["K_rot"] == pytest.approx(o1["K_rot"], rel=1e-6)
         assert o_b["U_lrc"] == pytest.approx(o1["U_lrc"], rel=1e-12)
 
 
@@ -143,8 +153,9 @@ def test_batch_argument_errors():
 def test_batch_nvt_matches_single_systems(use_graph):
     """Per-replica velocity rescaling (§2 NVT): the batched step with a
     target per replica (one replica left NVE) equals each replica's own
-    md_step with that target, and each thermostatted replica's half-step
-    temperature equals its target."""
+    md_step with that target (to the rounding of the batch's FP32 force
+    records), and each thermostatted replica's half-step temperature equals
+    its target."""
     from test_oracle_pins import _half_step_temperature
     cfgs = _replicas(n_rep=5, seed_k=11)
     targets = [0.8, 1.5, 0.0, 1.1, 2.0]
@@ -158,11 +169,16 @@ def test_batch_nvt_matches_single_systems(use_graph):
         s.set(c["r"], c["q"], c["v"], c["j"])
         s.step(6, 0.001, T_target=T)
         r1, v1, q1, j1 = s.molecules()
+        F1, t1 = s.forces()
         s.close()
         L = np.array(c["box"])
         dr = r - r1
         dr -= L * np.rint(dr / L)
-        assert np.abs(dr).max() < 1e-11 and np.abs(v - v1).max() < 1e-9 and np.abs(j - j1).max() < 1e-9
+        # FP32 records in the batch, FP64 totals in the single system (the
+        # bound of test_batch_equals_single_systems)
+        dv_tol = 1e-6 * 6 * 0.001 * np.abs(F1).max() / mdgen.model_mass(c["model"])
+        assert np.abs(v - v1).max() < dv_tol and np.abs(dr).max() < 6 * 0.001 * dv_tol
+        assert np.abs(j - j1).max() < 1e-6 * 6 * 0.001 * np.abs(t1).max()
         if T > 0:
             assert _half_step_temperature(c["model"], v, q, j) == pytest.approx(T, rel=1e-6)
 

@@ -403,14 +403,26 @@ def _energy_series(run_chunk, n_chunks):
     return np.array(E)
 
 
-def test_nve_energy_drift_1000_steps():
-    """LJTS fluid (N = 4096, T = 0.95, dt = 0.002) for 1000 leapfrog steps:
-    the total energy of the GPU path drifts no more than the FP64 oracle's
-    own drift plus three times the oracle's energy fluctuation (linear fit
-    over the 1000 steps; the trajectories themselves diverge, as chaotic
-    trajectories do, once rounding differs)."""
-    cfg = mdgen.config_lj_fluid(n=4096)
-    dt, every, n_chunks = cfg["dt"], 10, 100
+def equilibrated_2cljq(n=4000, seed_k=0):
+    """The 2CLJQ fluid (rho = 0.55, T = 1, rc = 3) after the untimed warm-up
+    of the measurement recipe, run by the FP64 oracle: 200 velocity-rescaled
+    steps at dt / 10, then 100 at dt (dt = 0.001)."""
+    cfg = mdgen.config_2cljq(n=n, seed_k=seed_k)
+    setup = oracle.setup_from_config(cfg)
+    st = {k: cfg[k] for k in ("r", "v", "q", "j")}
+    st = oracle.step(cfg["model"], setup, st, cfg["dt"] / 10, 200, use_cells=True, T_target=cfg["T"])
+    st = oracle.step(cfg["model"], setup, st, cfg["dt"], 100, use_cells=True, T_target=cfg["T"])
+    out = dict(cfg)
+    out.update({k: st[k] for k in ("r", "v", "q", "j")})
+    return out
+
+
+def nve_drift(cfg, n_steps=1000, every=10):
+    """Total energy U + K_trans + K_rot every `every` steps over n_steps NVE
+    leapfrog steps, GPU (deterministic full shell) and FP64 oracle from the
+    same start; returns (drift_gpu, drift_oracle, rms_fluct_oracle) over the
+    run (linear fits) and the per-step-per-molecule drifts."""
+    dt, n_chunks = cfg["dt"], n_steps // every
     s = md.System(cfg, deterministic=1)
     s.set(cfg["r"], cfg["q"], cfg["v"], cfg["j"])
 
@@ -432,12 +444,26 @@ def test_nve_energy_drift_1000_steps():
     t = np.arange(1, n_chunks + 1) * every * dt
     fit_g, fit_o = np.polyfit(t, Eg, 1), np.polyfit(t, Eo, 1)
     span = t[-1] - t[0]
-    drift_g, drift_o = fit_g[0] * span, fit_o[0] * span
-    rms_o = float(np.std(Eo - np.polyval(fit_o, t)))
-    _log(case="nve-drift/lj-4096", steps=n_chunks * every, drift_gpu=float(drift_g), drift_oracle=float(drift_o),
-         rms_fluct_oracle=rms_o, drift_gpu_per_step_per_mol=float(fit_g[0] * dt / 4096),
-         drift_oracle_per_step_per_mol=float(fit_o[0] * dt / 4096))
-    assert abs(drift_g) <= abs(drift_o) + 3.0 * rms_o + 1e-9 * abs(Eo).max()
+    n = cfg["r"].shape[0]
+    return {"drift_gpu": float(fit_g[0] * span), "drift_oracle": float(fit_o[0] * span),
+            "rms_fluct_oracle": float(np.std(Eo - np.polyval(fit_o, t))), "E_scale": float(np.abs(Eo).max()),
+            "drift_gpu_per_step_per_mol": float(fit_g[0] * dt / n),
+            "drift_oracle_per_step_per_mol": float(fit_o[0] * dt / n), "steps": n_steps}
+
+
+@pytest.mark.parametrize("which", ["lj-4096", "2cljq-4000"])
+def test_nve_energy_drift_1000_steps(which):
+    """1000 NVE leapfrog steps: the total energy of the GPU path drifts no
+    more than the FP64 oracle's own drift plus three times the oracle's
+    energy fluctuation (linear fits over the run; the trajectories
+    themselves diverge, as chaotic trajectories do, once rounding differs).
+    LJTS fluid (N = 4096, T = 0.95, dt = 0.002, no rotation) and the rigid
+    2CLJQ fluid (N = 4000, dt = 0.001, the rotational leapfrog of Eqs. 4-5
+    in play) started from its oracle-equilibrated state."""
+    cfg = mdgen.config_lj_fluid(n=4096) if which == "lj-4096" else equilibrated_2cljq(4000)
+    d = nve_drift(cfg)
+    _log(case=f"nve-drift/{which}", **d)
+    assert abs(d["drift_gpu"]) <= abs(d["drift_oracle"]) + 3.0 * d["rms_fluct_oracle"] + 1e-9 * d["E_scale"], d
 
 
 # ------------------------------------- models outside the compiled signatures
