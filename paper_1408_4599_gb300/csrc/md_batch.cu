@@ -193,7 +193,7 @@ struct BatchArgs {
 template <class SIG, bool HALF>
 __global__ void __launch_bounds__(MD_WARPS * 32) k_force_batch(const __grid_constant__ BatchArgs B)
 {
-    using Op = ForceOp<SIG, HALF>;
+    using Op = ForceOp<SIG, HALF, false>;  // chunked half shell (see ForceOp)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     typename Op::Tile *T = reinterpret_cast<typename Op::Tile *>(smem_raw) + warp;
@@ -358,7 +358,7 @@ struct LaunchBatchForce {
     cudaError_t run() const
     {
         if (B.n_work == 0) return cudaSuccess;
-        const size_t sm = sizeof(typename ForceOp<SIG, HALF>::Tile) * MD_WARPS;
+        const size_t sm = sizeof(typename ForceOp<SIG, HALF, false>::Tile) * MD_WARPS;
         cudaFuncSetAttribute(k_force_batch<SIG, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         int per_sm = 0, dev = 0, sms = 0;
         cudaGetDevice(&dev);

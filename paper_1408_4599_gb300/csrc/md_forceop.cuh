@@ -39,14 +39,19 @@ struct ForceExtra {
     double tot[5][32];
 };
 
-template <class SIG, bool HALF>
+// RUNS_: drain the half shell in runs (single systems); false keeps the
+// chunked pipeline with per-pair reductions on both molecules, which the
+// batched replicas use: their many small and dilute cells pay the larger
+// staging area and the per-window drain of the run-drained form (measured
+// 44% slower batched force evaluations).
+template <class SIG, bool HALF, bool RUNS_ = HALF>
 struct ForceOp {
     static constexpr int IMAX = 32;
     static constexpr int NQ = SIG::SINGLE ? 3 : 6;  // accumulated values per molecule: F, and tau unless single-site
     // the half shell is drained in runs (drain): a lane keeps its i's force
     // and torque in registers over consecutive pairs of that i
-    static constexpr bool RUNS = HALF;
-    using Tile = std::conditional_t<HALF, WarpTileD<ForceExtraHalf, QRUN>, WarpTile<ForceExtra, QCAP>>;
+    static constexpr bool RUNS = HALF && RUNS_;
+    using Tile = std::conditional_t<RUNS, WarpTileD<ForceExtraHalf, QRUN>, WarpTile<ForceExtra, QCAP>>;
     const DevModel &m;
     const ForceArgs &A;
     int K;
@@ -54,8 +59,8 @@ struct ForceOp {
     float pF0, pF1, pF2, pT0, pT1, pT2;            // the lane's pair of the current chunk (i side)
     float tq0, tq1, tq2;                           // its torque on j (half shell)
     int pjs, psi;                                  // storage slots of its j and i
-    float cU, cW, cX, cY, cZ;                      // pass sums of energy and virial (FP32)
-    int nmol, nexam;
+    float cU, cW, cX, cY, cZ;                      // lane sums of energy and virial since the last FP64 flush
+    int nmol, nexam, nflush;
     Tile *T;
     int ln;                                        // the lane (index of its compensated totals)
 
@@ -70,19 +75,27 @@ struct ForceOp {
     {
 #pragma unroll
         for (int q = 0; q < 5; q++) T->x.tot[q][ln] = 0.0;
-        nmol = nexam = 0;
+        cU = cW = cX = cY = cZ = 0.f;
+        nmol = nexam = nflush = 0;
     }
     // the lane's total of value q (0 U, 1 W, 2 W_xx, 3 W_yy, 4 W_zz)
-    __device__ double total(int q) const { return T->x.tot[q][ln]; }
+    __device__ double total(int q) const
+    {
+        const float c5[5] = {cU, cW, cX, cY, cZ};
+        return T->x.tot[q][ln] + (double)c5[q];
+    }
     __device__ void pass_begin(int ig_, int ni, int lane)
     {
         ig = ig_;
         if constexpr (!HALF) {  // the half shell sums its i terms while draining
+            float *f = reinterpret_cast<float *>(&T->x.it[0][0]);  // FP32 view (to_acc)
             for (int t = lane; t < ni; t += 32)
 #pragma unroll
-                for (int q = 0; q < 6; q++) T->x.it[q][t] = 0.0;
+                for (int q = 0; q < 6; q++) {
+                    if (A.to_acc) f[q * 32 + t] = 0.f;
+                    else T->x.it[q][t] = 0.0;
+                }
         }
-        cU = cW = cX = cY = cZ = 0.f;
     }
     __device__ void seg_begin(Tile &, int, int) {}
     __device__ void count_examined(int n) { nexam += n; }
@@ -110,13 +123,23 @@ struct ForceOp {
             tq2 = tq[2];
         }
     }
-    // End of a chunk (full shell, deterministic; the half shell is drained
-    // in runs): a segmented suffix sum over the lanes, the first lane of each
-    // i adding the i's total to the pass totals in shared memory.
+    // End of a chunk.  Chunked half shell: each lane adds its pair's terms
+    // straight to the FP32 records of i and j (a 16-byte vector reduction
+    // for F and one for tau per molecule).  Full shell (deterministic): a
+    // segmented suffix sum over the lanes, the first lane of each i adding
+    // the i's total to the pass totals in shared memory.
     __device__ void chunk_end(Tile &, int il, int, bool valid, int lane)
     {
-        if constexpr (HALF) return;
-        else {
+        if constexpr (HALF) {
+            if (valid) {
+                float *a = A.acc + (long long)FACC_STRIDE * psi;
+                red_add_v4(a, pF0, pF1, pF2, 0.f);
+                if (NQ == 6) red_add_v4(a + 4, pT0, pT1, pT2, 0.f);
+                float *b = A.acc + (long long)FACC_STRIDE * pjs;
+                red_add_v4(b, -pF0, -pF1, -pF2, 0.f);
+                if (NQ == 6) red_add_v4(b + 4, tq0, tq1, tq2, 0.f);
+            }
+        } else {
         const int nvalid = __popc(__ballot_sync(FULLMASK, valid));  // valid lanes are a prefix
         const int prev = __shfl_up_sync(FULLMASK, il, 1);
         const bool head = valid && (lane == 0 || prev != il);
@@ -134,9 +157,15 @@ struct ForceOp {
                 if (take) v[q] += o;
             }
         }
-        if (head) {  // the segment's FP32 sum (<= 32 pair terms) joins the i's FP64 total
+        if (head) {  // the segment's FP32 sum (<= 32 pair terms) joins the i's total
+            if (A.to_acc) {  // destined for FP32 records (batched replicas): FP32 totals
+                float *f = reinterpret_cast<float *>(&T->x.it[0][0]);
 #pragma unroll
-            for (int q = 0; q < NQ; q++) T->x.it[q][il] += (double)v[q];
+                for (int q = 0; q < NQ; q++) f[q * 32 + il] += v[q];
+            } else {  // FP64 outputs: FP64 totals
+#pragma unroll
+                for (int q = 0; q < NQ; q++) T->x.it[q][il] += (double)v[q];
+            }
         }
         }
     }
@@ -221,14 +250,15 @@ struct ForceOp {
         if constexpr (!HALF) {
             for (int t = lane; t < ni; t += 32) {
                 const int si = s0 + ig_ + t;
-                double ip[6];
-#pragma unroll
-                for (int q = 0; q < 6; q++) ip[q] = T->x.it[q][t];
                 if (A.to_acc) {
+                    const float *f = reinterpret_cast<const float *>(&T->x.it[0][0]);
                     float *a = A.acc + (long long)FACC_STRIDE * si;
-                    red_add_v4(a, (float)ip[0], (float)ip[1], (float)ip[2], 0.f);
-                    if (NQ == 6) red_add_v4(a + 4, (float)ip[3], (float)ip[4], (float)ip[5], 0.f);
+                    red_add_v4(a, f[t], f[32 + t], f[64 + t], 0.f);
+                    if (NQ == 6) red_add_v4(a + 4, f[96 + t], f[128 + t], f[160 + t], 0.f);
                 } else {
+                    double ip[6];
+#pragma unroll
+                    for (int q = 0; q < 6; q++) ip[q] = T->x.it[q][t];
                     double *Fo = A.F + 3LL * si, *To = A.tau + 3LL * si;
                     const double t0 = NQ == 6 ? ip[3] : 0.0, t1 = NQ == 6 ? ip[4] : 0.0, t2 = NQ == 6 ? ip[5] : 0.0;
                     Fo[0] = ip[0];
@@ -243,10 +273,16 @@ struct ForceOp {
                 }
             }
         }
-        // the pass's FP32 lane sums join the lane's FP64 totals
-        const float c5[5] = {cU, cW, cX, cY, cZ};
+        // the lane's FP32 sums join its FP64 totals once they hold >= 256
+        // pair terms (one FP64 add per value then; sparse cells would
+        // otherwise pay it per pass)
+        if (nmol - nflush >= 256) {
+            const float c5[5] = {cU, cW, cX, cY, cZ};
 #pragma unroll
-        for (int q = 0; q < 5; q++) T->x.tot[q][ln] += (double)c5[q];
+            for (int q = 0; q < 5; q++) T->x.tot[q][ln] += (double)c5[q];
+            cU = cW = cX = cY = cZ = 0.f;
+            nflush = nmol;
+        }
     }
 };
 
@@ -254,12 +290,18 @@ struct ForceOp {
 // Warp totals of the energy / virial sums and pair counts of one op (all
 // lanes return the same values).
 template <class Op>
+// Used per cell by the batched kernel: the lane totals of one cell are sums
+// of a few hundred FP32 pair terms, so the warp sum is taken in FP32 (FP64
+// shuffles and adds per cell measured 50% slower batched force
+// evaluations); the per-replica sums are FP64.
 __device__ __forceinline__ void op_warp_totals(Op &op, double (&v)[5], int &nm, int &ne)
 {
 #pragma unroll
-    for (int q = 0; q < 5; q++) v[q] = op.total(q);
-    for (int q = 0; q < 5; q++)
-        for (int msk = 16; msk > 0; msk >>= 1) v[q] += __shfl_xor_sync(FULLMASK, v[q], msk);
+    for (int q = 0; q < 5; q++) {
+        float f = (float)op.total(q);
+        for (int msk = 16; msk > 0; msk >>= 1) f += __shfl_xor_sync(FULLMASK, f, msk);
+        v[q] = f;
+    }
     nm = __reduce_add_sync(FULLMASK, op.nmol);
     ne = __reduce_add_sync(FULLMASK, op.nexam);
 }
