@@ -535,7 +535,7 @@ md_status do_rebuild(md_system *s, cudaStream_t st, bool need_cellid, const doub
 {
     TimeScope ts(s, st, 1);
     if (need_cellid) CK(launch_cellid(s->g, s->d, st), "cell id kernel");
-    CK(launch_rebuild(s->g, s->m, s->d, st, beta), "cell rebuild kernels");
+    CK(launch_rebuild(s->g, s->m, s->d, st, beta, s->opt.deterministic), "cell rebuild kernels");
     s->binned = true;
     return MD_OK;
 }
@@ -561,7 +561,8 @@ md_status one_step(md_system *s, double dt, double T_target, cudaStream_t st)
     const bool thermo = nvt && dof > 0.0 && s->d.n > 0;
     {
         TimeScope ts(s, st, 0);
-        CK(launch_integrate(s->g, s->m, s->d, dt, s->half_eff, st), "integrate kernel");
+        // a non-deterministic rebuild leaves the histogram at zero
+        CK(launch_integrate(s->g, s->m, s->d, dt, s->half_eff, st, s->opt.deterministic), "integrate kernel");
         if (thermo) CK(launch_thermostat(s->m, s->d, s->n_kin_blocks, T_target, dof, st), "thermostat kernels");
     }
     md_status ms = do_rebuild(s, st, false, thermo ? s->d.thermo : nullptr);

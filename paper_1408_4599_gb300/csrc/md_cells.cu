@@ -137,6 +137,33 @@ __global__ void k_scan_down(const int *count, long long ncell, const int *block_
     if (base <= ncell - 1 && ncell - 1 < base + SCAN_ITEMS) start[ncell] = ex;
 }
 
+// Exclusive scan of the histogram by one block, tile after tile (grids of
+// up to SCAN_SINGLE_MAX cells: one launch instead of three).
+constexpr long long SCAN_SINGLE_MAX = 16LL * SCAN_TILE;
+
+__global__ void k_scan_single(const int *count, long long ncell, int *start)
+{
+    __shared__ int sw[32];
+    int carry = 0;
+    for (long long t0 = 0; t0 < ncell; t0 += SCAN_TILE) {
+        const long long base = t0 + threadIdx.x * SCAN_ITEMS;
+        int loc[SCAN_ITEMS];
+        int v = 0;
+        for (int k = 0; k < SCAN_ITEMS; k++) {
+            loc[k] = (base + k < ncell) ? count[base + k] : 0;
+            v += loc[k];
+        }
+        int total;
+        int ex = block_exclusive_scan(v, sw, total) + carry;
+        for (int k = 0; k < SCAN_ITEMS; k++) {
+            if (base + k < ncell) start[base + k] = ex;
+            ex += loc[k];
+        }
+        carry += total;
+    }
+    if (threadIdx.x == 0) start[ncell] = carry;
+}
+
 // Counting-sort scatter: unstable slot claim inside each cell.
 __global__ void k_scatter(const int *cell, const int *start, int *fill, int *perm, long long n)
 {
@@ -171,31 +198,12 @@ __global__ void k_sort_cells(const int *start, const int *perm, const int *ids, 
     }
 }
 
-// Reorder the FP64 state into the new cell order and pack the FP32 data
-// of the force kernel: the centre of mass relative to its cell centre
-// (formed in FP64, then rounded) and the space-frame site offsets and axes
-// R(q) d, R(q) e.
-__global__ void k_reorder_pack(Grid g, DevModel m, DevState d, const double *beta)
+// The FP32 data the force kernel reads for the molecule in slot s of cell
+// c: its centre of mass relative to the cell centre (formed in FP64, then
+// rounded) and the space-frame site offsets and axes R(q) d, R(q) e.
+__device__ __forceinline__ void pack_one(const Grid &g, const DevModel &m, const DevState &d, long long s, int c,
+                                         double rx, double ry, double rz, double qw, double qx, double qy, double qz)
 {
-    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= d.n) return;
-    int o = d.perm2[s];
-    const double b = beta ? *beta : 1.0;  // velocity-rescaling factor of this step
-    double rx = d.r[3 * o], ry = d.r[3 * o + 1], rz = d.r[3 * o + 2];
-    d.r2[3 * s] = rx;
-    d.r2[3 * s + 1] = ry;
-    d.r2[3 * s + 2] = rz;
-    for (int k = 0; k < 3; k++) {
-        d.v2[3 * s + k] = b * d.v[3 * o + k];
-        d.j2[3 * s + k] = b * d.j[3 * o + k];
-    }
-    // quaternion records are 32-byte aligned: two 16-byte moves
-    const double2 q01 = reinterpret_cast<const double2 *>(d.q)[2 * o], q23 = reinterpret_cast<const double2 *>(d.q)[2 * o + 1];
-    reinterpret_cast<double2 *>(d.q2)[2 * s] = q01;
-    reinterpret_cast<double2 *>(d.q2)[2 * s + 1] = q23;
-    const double qw = q01.x, qx = q01.y, qy = q23.x, qz = q23.y;
-    d.ids2[s] = d.ids[o];
-    int c = d.cell[o];
     int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
     float4 cm;
     cm.x = (float)(rx - (cx + 0.5) * g.ell[0]);
@@ -224,6 +232,58 @@ __global__ void k_reorder_pack(Grid g, DevModel m, DevState d, const double *bet
                             R[6] * e[0] + R[7] * e[1] + R[8] * e[2], 0.0f);
         }
     }
+}
+
+// Reorder the FP64 state into the new cell order (new slot s <- old slot
+// perm2[s]) and pack the force kernel's FP32 data.
+__global__ void k_reorder_pack(Grid g, DevModel m, DevState d, const double *beta)
+{
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.n) return;
+    int o = d.perm2[s];
+    const double b = beta ? *beta : 1.0;  // velocity-rescaling factor of this step
+    double rx = d.r[3 * o], ry = d.r[3 * o + 1], rz = d.r[3 * o + 2];
+    d.r2[3 * s] = rx;
+    d.r2[3 * s + 1] = ry;
+    d.r2[3 * s + 2] = rz;
+    for (int k = 0; k < 3; k++) {
+        d.v2[3 * s + k] = b * d.v[3 * o + k];
+        d.j2[3 * s + k] = b * d.j[3 * o + k];
+    }
+    // quaternion records are 32-byte aligned: two 16-byte moves
+    const double2 q01 = reinterpret_cast<const double2 *>(d.q)[2 * o], q23 = reinterpret_cast<const double2 *>(d.q)[2 * o + 1];
+    reinterpret_cast<double2 *>(d.q2)[2 * s] = q01;
+    reinterpret_cast<double2 *>(d.q2)[2 * s + 1] = q23;
+    d.ids2[s] = d.ids[o];
+    pack_one(g, m, d, s, d.cell[o], rx, ry, rz, q01.x, q01.y, q23.x, q23.y);
+}
+
+// Counting-sort scatter fused with the reorder and packing (runs without
+// the deterministic in-cell order): old slot s claims a slot of its cell by
+// counting the cell's histogram entry down (which leaves the histogram at
+// zero for the next step) and writes its whole record there.  The reads
+// are in storage order; the writes land near s, since molecules rarely
+// change cell in one step.
+__global__ void k_scatter_pack(Grid g, DevModel m, DevState d, const double *beta)
+{
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.n) return;
+    const int c = d.cell[s];
+    const long long p = d.cell_start[c] + atomicSub(&d.cell_count[c], 1) - 1;
+    const double b = beta ? *beta : 1.0;
+    const double rx = d.r[3 * s], ry = d.r[3 * s + 1], rz = d.r[3 * s + 2];
+    d.r2[3 * p] = rx;
+    d.r2[3 * p + 1] = ry;
+    d.r2[3 * p + 2] = rz;
+    for (int k = 0; k < 3; k++) {
+        d.v2[3 * p + k] = b * d.v[3 * s + k];
+        d.j2[3 * p + k] = b * d.j[3 * s + k];
+    }
+    const double2 q01 = reinterpret_cast<const double2 *>(d.q)[2 * s], q23 = reinterpret_cast<const double2 *>(d.q)[2 * s + 1];
+    reinterpret_cast<double2 *>(d.q2)[2 * p] = q01;
+    reinterpret_cast<double2 *>(d.q2)[2 * p + 1] = q23;
+    d.ids2[p] = d.ids[s];
+    pack_one(g, m, d, p, c, rx, ry, rz, q01.x, q01.y, q23.x, q23.y);
 }
 
 __global__ void k_scatter_out(const int *ids, const double *src, int width, double *dst, long long n)
@@ -258,14 +318,24 @@ cudaError_t launch_cellid(const Grid &g, DevState &d, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Counting sort over ncell cells: scan of the histogram, scatter and the
-// in-cell sort; leaves the new order (new slot -> old slot) in perm2.
-cudaError_t launch_sort(long long ncell, DevState &d, cudaStream_t s)
+// Exclusive scan of the histogram into cell_start (ncell + 1 entries).
+static void launch_scan(long long ncell, DevState &d, cudaStream_t s)
 {
+    if (ncell <= SCAN_SINGLE_MAX) {
+        k_scan_single<<<1, SCAN_THREADS, 0, s>>>(d.cell_count, ncell, d.cell_start);
+        return;
+    }
     int nb = scan_blocks(ncell);
     k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(d.cell_count, ncell, d.scan_tmp);
     k_scan_top<<<1, SCAN_THREADS, 0, s>>>(d.scan_tmp, nb);
     k_scan_down<<<nb, SCAN_THREADS, 0, s>>>(d.cell_count, ncell, d.scan_tmp, d.cell_start);
+}
+
+// Counting sort over ncell cells: scan of the histogram, scatter and the
+// in-cell sort; leaves the new order (new slot -> old slot) in perm2.
+cudaError_t launch_sort(long long ncell, DevState &d, cudaStream_t s)
+{
+    launch_scan(ncell, d, s);
     cudaError_t e = cudaMemsetAsync(d.cell_fill, 0, sizeof(int) * ncell, s);
     if (e != cudaSuccess) return e;
     if (d.n > 0) {
@@ -288,11 +358,21 @@ void swap_state(DevState &d)
 
 // Scan of the histogram, scatter, in-cell sort, reorder + pack, then swap
 // the state buffers.  Expects cell[] and cell_count[] of the current order.
-cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaStream_t s, const double *beta)
+// deterministic = 0: the scatter claims slots by counting the histogram
+// down and writes the records itself (no in-cell sort, no separate
+// reorder), leaving cell_count at zero.
+cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaStream_t s, const double *beta,
+                           int deterministic)
 {
-    cudaError_t e = launch_sort(g.ncell, d, s);
-    if (e != cudaSuccess) return e;
-    if (d.n > 0) k_reorder_pack<<<nblk(d.n, 256), 256, 0, s>>>(g, m, d, beta);
+    cudaError_t e = cudaSuccess;
+    if (deterministic) {
+        e = launch_sort(g.ncell, d, s);
+        if (e != cudaSuccess) return e;
+        if (d.n > 0) k_reorder_pack<<<nblk(d.n, 256), 256, 0, s>>>(g, m, d, beta);
+    } else {
+        launch_scan(g.ncell, d, s);
+        if (d.n > 0) k_scatter_pack<<<nblk(d.n, 256), 256, 0, s>>>(g, m, d, beta);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     double *t;

@@ -126,9 +126,10 @@ __global__ void k_rescale(DevState d, double fv, double fj)
 
 }  // namespace
 
-cudaError_t launch_integrate(const Grid &g, const DevModel &m, DevState &d, double dt, int acc32, cudaStream_t s)
+cudaError_t launch_integrate(const Grid &g, const DevModel &m, DevState &d, double dt, int acc32, cudaStream_t s,
+                             int zero_count)
 {
-    cudaError_t e = cudaMemsetAsync(d.cell_count, 0, sizeof(int) * g.ncell, s);
+    cudaError_t e = zero_count ? cudaMemsetAsync(d.cell_count, 0, sizeof(int) * g.ncell, s) : cudaSuccess;
     if (e != cudaSuccess || d.n == 0) return e;
     const LeapArgs a = leap_args(m, dt);
     const unsigned nb = (unsigned)((d.n + 127) / 128);

@@ -112,15 +112,18 @@ enum { FLAG_NONFINITE = 0, FLAG_OVERFLOW = 1, FLAG_TIMEOUT = 2, FLAG_INPUT = 3 }
 cudaError_t launch_cellid(const Grid &g, DevState &d, cudaStream_t s);
 // beta (device scalar, may be NULL): factor applied to v and j while they are reordered
 cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaStream_t s,
-                           const double *beta = nullptr);
+                           const double *beta = nullptr, int deterministic = 1);
 cudaError_t launch_sort(long long ncell, DevState &d, cudaStream_t s);
 void swap_state(DevState &d);
 // half shell: the results stay in the FP32 accumulators d.facc until
 // launch_force_finalize; full shell: FP64 d.F, d.tau directly.
 cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half_shell, int dynamic_cells, int n_blocks,
                          cudaStream_t s);
-// acc32: read the forces from d.facc instead of d.F, d.tau
-cudaError_t launch_integrate(const Grid &g, const DevModel &m, DevState &d, double dt, int acc32, cudaStream_t s);
+// acc32: read the forces from d.facc instead of d.F, d.tau; zero_count:
+// clear the histogram first (not needed after a non-deterministic rebuild,
+// which leaves it at zero)
+cudaError_t launch_integrate(const Grid &g, const DevModel &m, DevState &d, double dt, int acc32, cudaStream_t s,
+                             int zero_count = 1);
 cudaError_t launch_kinetic(const DevModel &m, DevState &d, double dt_half, int n_blocks, cudaStream_t s);
 cudaError_t launch_rescale(const DevModel &m, DevState &d, double fac_v, double fac_j, cudaStream_t s);
 // velocity rescaling to T_target: half-step kinetic energies -> d.thermo[0] = sqrt(T_target / T_half)
