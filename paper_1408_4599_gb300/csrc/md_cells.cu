@@ -264,20 +264,28 @@ __global__ void k_reorder_pack(Grid g, DevModel m, DevState d, const double *bet
 // zero for the next step) and writes its whole record there.  The reads
 // are in storage order; the writes land near s, since molecules rarely
 // change cell in one step.
+template <bool BETA>  // BETA: apply the velocity-rescaling factor (NVT steps)
 __global__ void k_scatter_pack(Grid g, DevModel m, DevState d, const double *beta)
 {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= d.n) return;
     const int c = d.cell[s];
     const long long p = d.cell_start[c] + atomicSub(&d.cell_count[c], 1) - 1;
-    const double b = beta ? *beta : 1.0;
     const double rx = d.r[3 * s], ry = d.r[3 * s + 1], rz = d.r[3 * s + 2];
     d.r2[3 * p] = rx;
     d.r2[3 * p + 1] = ry;
     d.r2[3 * p + 2] = rz;
-    for (int k = 0; k < 3; k++) {
-        d.v2[3 * p + k] = b * d.v[3 * s + k];
-        d.j2[3 * p + k] = b * d.j[3 * s + k];
+    if constexpr (BETA) {
+        const double b = *beta;
+        for (int k = 0; k < 3; k++) {
+            d.v2[3 * p + k] = b * d.v[3 * s + k];
+            d.j2[3 * p + k] = b * d.j[3 * s + k];
+        }
+    } else {  // (FP64 multiplies run at a small fraction of the FP32 rate)
+        for (int k = 0; k < 3; k++) {
+            d.v2[3 * p + k] = d.v[3 * s + k];
+            d.j2[3 * p + k] = d.j[3 * s + k];
+        }
     }
     const double2 q01 = reinterpret_cast<const double2 *>(d.q)[2 * s], q23 = reinterpret_cast<const double2 *>(d.q)[2 * s + 1];
     reinterpret_cast<double2 *>(d.q2)[2 * p] = q01;
@@ -371,7 +379,10 @@ cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaSt
         if (d.n > 0) k_reorder_pack<<<nblk(d.n, 256), 256, 0, s>>>(g, m, d, beta);
     } else {
         launch_scan(g.ncell, d, s);
-        if (d.n > 0) k_scatter_pack<<<nblk(d.n, 256), 256, 0, s>>>(g, m, d, beta);
+        if (d.n > 0) {
+            if (beta) k_scatter_pack<true><<<nblk(d.n, 256), 256, 0, s>>>(g, m, d, beta);
+            else k_scatter_pack<false><<<nblk(d.n, 256), 256, 0, s>>>(g, m, d, beta);
+        }
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
