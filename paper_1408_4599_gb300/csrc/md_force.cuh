@@ -51,14 +51,16 @@ constexpr int force_min_blocks()
 template <class SIG, bool HALF, int M>
 constexpr size_t force_smem()
 {
-    return sizeof(typename ForceOp<SIG, HALF>::Tile) * MD_WARPS + (M == 2 ? sizeof(StencilMeta) * MD_WARPS : 0);
+    return sizeof(typename ForceOp<SIG, HALF, M == 1>::Tile) * MD_WARPS + (M == 2 ? sizeof(StencilMeta) * MD_WARPS : 0);
 }
 
 // M: stencil radius in cells (1: cells of edge >= r_c; 2: >= r_c / 2).
 template <class SIG, bool HALF, int M>
 __global__ void __launch_bounds__(MD_WARPS * 32, force_min_blocks<SIG, HALF>()) k_force(const __grid_constant__ ForceArgs A)
 {
-    using Op = ForceOp<SIG, HALF>;
+    // cells of edge >= r_c / 2 hold ~2 molecules: the chunked half shell
+    // (the run-drained form's per-window costs measured 2.5-5.6x slower there)
+    using Op = ForceOp<SIG, HALF, M == 1>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     typename Op::Tile *T = reinterpret_cast<typename Op::Tile *>(smem_raw) + warp;
