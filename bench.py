@@ -662,7 +662,10 @@ def run_batch(args, md, torch, dev, rank):
     b.set_thermostat(temps)
     b.step(100, dt / 10, use_graph=True)
     b.step(100, dt, use_graph=True)
-    tune = b.tune()
+    # tiles: work chunk x grid share x test width x shell policy, cached per
+    # GPU, site signature and occupancy bucket
+    tune = b.tune_tiles(os.path.join(ROOT, "paper_1408_4599_gb300", "_tune_cache.txt"))
+    tune["gain_over_default"] = tune["default_ms"] / tune["ms"] if tune["ms"] > 0 else None
     b.step(args.warmup, dt, use_graph=True)
     o0 = b.observables()
     clocks = ClockSampler(dev)

@@ -271,10 +271,31 @@ md_status md_batch_get_molecules(md_batch *b, double *r, double *v, double *q, d
                                  void *cuda_stream);
 md_status md_batch_get_forces(md_batch *b, double *F, double *tau, int32_t on_device, void *cuda_stream);
 
-/* Autotuner: times the batched force evaluation for each work-chunk size
- * (1, 2, 4, 8, 16 cells per queue grab) and grid occupancy (100% or 50% of
- * the resident blocks) with CUDA events and keeps the fastest.  Outputs may
- * be NULL.  Synchronising. */
+/* Tiles of the batched force evaluation (§4: the same cost model orders
+ * the work; these choose how it is cut). */
+typedef struct {
+    int32_t chunk;        /* cells per work-queue grab: 1, 2, 4 or 8 */
+    int32_t grid_pct;     /* launched share of the resident blocks: 100 or 50 */
+    int32_t test_width;   /* candidates per lane per distance-test round: 4 or 8 */
+    double half_min_occ;  /* replicas whose mean occupancy (molecules per cell) is below this run the full
+                           * 27-cell stencil instead of the Newton-3 half stencil: 0, 2 or 6 */
+    float ms;             /* batched force evaluation with the chosen tiles (mean of 3, CUDA events) */
+    float default_ms;     /* the same with the defaults (chunk 2, 100%, 8, 0) */
+    int32_t from_cache;   /* 1: the choice came from the tuning cache, not from timing */
+    char key[160];        /* cache key: GPU name | site signature | occupancy bucket (half-octaves) */
+} md_batch_tuning;
+
+/* Autotuner: times the batched force evaluation (CUDA events on
+ * cuda_stream) over work chunk x grid share x test width x shell policy
+ * (48 tile sets) and keeps the fastest.  cache_path (may be NULL): a text
+ * file of earlier choices keyed by out->key; a hit is applied without
+ * timing, a miss is timed and stored.  The default tile set is timed too
+ * (out->default_ms) for the comparison.  Captured step graphs are dropped.
+ * Synchronising.  Errors: MD_ERR_ARG (NULL b or out), MD_ERR_STATE (no
+ * molecules set), MD_ERR_CUDA. */
+md_status md_batch_tune_tiles(md_batch *b, void *cuda_stream, const char *cache_path, md_batch_tuning *out);
+
+/* The same without a cache; outputs may be NULL. */
 md_status md_batch_tune(md_batch *b, void *cuda_stream, int32_t *best_chunk, int32_t *best_grid_pct,
                         float *best_ms);
 

@@ -23,6 +23,7 @@
 #include <cstdio>
 #include <cstring>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "../../include/md.h"
@@ -34,7 +35,7 @@ using namespace mdk;
 // Per-replica grid on the device.
 struct RepGrid {
     int nc[3];
-    int half;  // 1: half stencil
+    int half;  // 1: half stencil (needs >= 3 cells per axis and options->half_shell; see half_min_occ)
     float ellf[3];
     double L[3];
     double ell[3];
@@ -49,8 +50,11 @@ struct md_batch {
     md_options opt;
     double rc = 0.0, lrc_u = 0.0, lrc_w = 0.0, rf_self = 0.0;
     std::vector<RepGrid> grids;
+    std::vector<char> half_ok;  // replica may use the half stencil
     std::vector<long long> n_per;
     std::vector<long long> cell_off;
+    std::vector<double> rep_cost;  // Eq. 6 cost estimate per replica
+    std::vector<int> work_host;    // host copy of the work list
     long long ncell = 0, ntot = 0, cap = 0;
     Grid g;  // shared scalars (rc2, band); ncell = total cells
     DevState d;
@@ -71,6 +75,8 @@ struct md_batch {
     double dt_last = 0.0, time = 0.0;
     long long step = 0;
     int chunk = 2, grid_frac_pct = 100;
+    int test_width = NTEST;     // candidates per lane per test round (4 or NTEST)
+    double half_min_occ = 0.0;  // replicas below this mean occupancy (molecules per cell) run the full shell
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     double gdt[2] = {0.0, 0.0};
     int parity = 0;
@@ -190,7 +196,7 @@ struct BatchArgs {
 };
 
 // Persistent force kernel over a work list of cells of many replicas.
-template <class SIG, bool HALF>
+template <class SIG, bool HALF, int NT>
 __global__ void __launch_bounds__(MD_WARPS * 32) k_force_batch(const __grid_constant__ BatchArgs B)
 {
     using Op = ForceOp<SIG, HALF, false>;  // chunked half shell (see ForceOp)
@@ -219,7 +225,8 @@ __global__ void __launch_bounds__(MD_WARPS * 32) k_force_batch(const __grid_cons
             gv.rc2f = B.f.g.rc2f;
             gv.bandf = B.f.g.bandf;
             gv.cell0 = rg.cell0;
-            traverse_cell<SIG, HALF>(m, gv, B.f.cell_start, B.f.com, B.f.geo, B.f.r, K, c - rg.cell0, *T, op, lane);
+            traverse_cell<SIG, HALF, 1, NT>(m, gv, B.f.cell_start, B.f.com, B.f.geo, B.f.r, K, c - rg.cell0, *T, op,
+                                            lane);
             double v[5];
             int nm, ne;
             op_warp_totals(op, v, nm, ne);
@@ -346,35 +353,69 @@ __global__ void k_rep_thermostat(const RepGrid *G, int n_sys, long long n, DevMo
 
 struct LaunchBatchForce {
     const BatchArgs &B;
-    int half, blocks_cap;
+    int half, blocks_cap, nt;
     cudaStream_t s;
     template <class SIG>
     cudaError_t operator()() const
     {
-        if (half) return run<SIG, true>();
-        return run<SIG, false>();
+        if (half) return nt == 4 ? run<SIG, true, 4>() : run<SIG, true, NTEST>();
+        return nt == 4 ? run<SIG, false, 4>() : run<SIG, false, NTEST>();
     }
-    template <class SIG, bool HALF>
+    template <class SIG, bool HALF, int NT>
     cudaError_t run() const
     {
         if (B.n_work == 0) return cudaSuccess;
         const size_t sm = sizeof(typename ForceOp<SIG, HALF, false>::Tile) * MD_WARPS;
-        cudaFuncSetAttribute(k_force_batch<SIG, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_force_batch<SIG, HALF, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         int per_sm = 0, dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_batch<SIG, HALF>, MD_WARPS * 32, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_batch<SIG, HALF, NT>, MD_WARPS * 32, sm);
         long long want = (long long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
         want = want * blocks_cap / 100;
         const long long need = (B.n_work + MD_WARPS - 1) / MD_WARPS;
         if (want > need) want = need;
         if (want < 1) want = 1;
-        k_force_batch<SIG, HALF><<<(unsigned)want, MD_WARPS * 32, sm, s>>>(B);
+        k_force_batch<SIG, HALF, NT><<<(unsigned)want, MD_WARPS * 32, sm, s>>>(B);
         return cudaGetLastError();
     }
 };
 
 void bset_err(md_batch *b, const char *msg) { snprintf(b->err, sizeof b->err, "%s", msg); }
+
+md_status bcuda(md_batch *b, cudaError_t e, const char *where);
+
+// Stencil of every replica (half where allowed and the replica's mean
+// occupancy is at least half_min_occ molecules per cell, full otherwise)
+// and the work list: half-stencil cells first, each list longest replica
+// first by the Eq. 6 cost; copies grids and list to the device on st.
+md_status apply_shell_policy(md_batch *b, cudaStream_t st)
+{
+    for (int k = 0; k < b->n_sys; k++) {
+        const double nce = (double)(b->cell_off[k + 1] - b->cell_off[k]);
+        const double occ = (double)b->n_per[k] / nce;
+        b->grids[k].half = (b->half_ok[k] && occ >= b->half_min_occ) ? 1 : 0;
+    }
+    std::vector<int> order(b->n_sys);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->rep_cost[a] > b->rep_cost[c]; });
+    b->work_host.clear();
+    b->work_host.reserve((size_t)b->ncell);
+    for (int pass = 1; pass >= 0; pass--)
+        for (int k : order)
+            if (b->grids[k].half == pass)
+                for (long long c = b->cell_off[k]; c < b->cell_off[k + 1]; c++) b->work_host.push_back((int)c);
+    b->n_work_half = 0;
+    for (int k = 0; k < b->n_sys; k++)
+        if (b->grids[k].half) b->n_work_half += b->cell_off[k + 1] - b->cell_off[k];
+    b->n_work_full = b->ncell - b->n_work_half;
+    cudaError_t e = cudaMemcpyAsync(b->dgrids, b->grids.data(), sizeof(RepGrid) * b->n_sys, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->work, b->work_host.data(), sizeof(int) * b->work_host.size(), cudaMemcpyHostToDevice, st);
+    // the host vectors must outlive the copies
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? MD_OK : bcuda(b, e, "copy grids / work list");
+}
 
 md_status bcuda(md_batch *b, cudaError_t e, const char *where)
 {
@@ -428,7 +469,7 @@ md_status batch_force(md_batch *b, cudaStream_t st)
     BCK(cudaMemsetAsync(b->counters, 0, 2 * sizeof(int), st), "zero work queues");
     for (int h = 1; h >= 0; h--) {
         BatchArgs B = batch_args(b, h == 1);
-        BCK(dispatch_sig(b->m, LaunchBatchForce{B, h, b->grid_frac_pct, st}), "batched force kernel");
+        BCK(dispatch_sig(b->m, LaunchBatchForce{B, h, b->grid_frac_pct, b->test_width, st}), "batched force kernel");
     }
     b->forces_valid = true;
     b->f_in_acc = true;
@@ -557,6 +598,7 @@ md_status md_batch_create(int32_t n_sys, const double *boxes, double cutoff, con
             all3 = all3 && g.nc[a] >= 3;
         }
         g.half = (opt.half_shell && all3) ? 1 : 0;
+        b->half_ok.push_back((char)g.half);
         g.cell0 = nc_tot;
         b->cell_off[k] = nc_tot;
         nc_tot += (long long)g.nc[0] * g.nc[1] * g.nc[2];
@@ -682,23 +724,12 @@ md_status md_batch_set_molecules(md_batch *b, const int64_t *n_per_sys, const do
         const double occ = (double)n_per_sys[k] / nce;  // mean molecules per cell
         cost[k] = nce * 0.5 * occ * (occ + 26.0 * occ);  // sum over cells of n_d (§4, Eq. 6)
     }
-    std::vector<int> order(b->n_sys);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-    std::vector<int> wl;
-    wl.reserve((size_t)b->ncell);
-    for (int pass = 1; pass >= 0; pass--)
-        for (int k : order)
-            if (b->grids[k].half == pass)
-                for (long long c = b->cell_off[k]; c < b->cell_off[k + 1]; c++) wl.push_back((int)c);
-    b->n_work_half = 0;
-    for (int k = 0; k < b->n_sys; k++)
-        if (b->grids[k].half) b->n_work_half += b->cell_off[k + 1] - b->cell_off[k];
-    b->n_work_full = b->ncell - b->n_work_half;
+    b->rep_cost = cost;
     cudaStream_t st0 = st;
-    BCK(cudaMemcpyAsync(b->dgrids, b->grids.data(), sizeof(RepGrid) * b->n_sys, cudaMemcpyHostToDevice, st0),
-        "copy grids");
-    BCK(cudaMemcpyAsync(b->work, wl.data(), sizeof(int) * wl.size(), cudaMemcpyHostToDevice, st0), "copy work list");
+    {
+        md_status wm = apply_shell_policy(b, st0);
+        if (wm != MD_OK) return wm;
+    }
     BCK(cudaMemcpyAsync(b->rep_of_slot, ros.data(), sizeof(int) * ros.size(), cudaMemcpyHostToDevice, st0),
         "copy slot map");
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -913,45 +944,161 @@ md_status md_batch_set_thermostat(md_batch *b, const double *T_target, void *cud
     return MD_OK;
 }
 
-md_status md_batch_tune(md_batch *b, void *cuda_stream, int32_t *best_chunk, int32_t *best_grid_pct, float *best_ms)
+// Key of the tuning cache: GPU name | site signature (roles and LJ types of
+// the merged sites) | occupancy bucket (half-octaves of the mean molecules
+// per cell over all replicas).
+static void tune_key(md_batch *b, char *key, size_t cap)
 {
-    if (!b) return MD_ERR_ARG;
+    cudaDeviceProp p;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) snprintf(p.name, sizeof p.name, "unknown");
+    unsigned sig = 0, ty = 0;
+    for (int a = 0; a < b->m.S && a < 8; a++) {
+        sig |= (unsigned)b->m.roles[a] << (4 * a);
+        ty |= (unsigned)(b->m.roles[a] & ROLE_LJ ? b->m.lj_type[a] : 0) << (4 * a);
+    }
+    const double occ = b->ncell > 0 ? (double)b->ntot / (double)b->ncell : 0.0;
+    const int bucket = occ > 0.0 ? (int)std::floor(2.0 * std::log2(occ)) : -99;
+    snprintf(key, cap, "%s|%08x.%08x|occ%d", p.name, sig, ty, bucket);
+    for (char *c = key; *c; c++)
+        if (*c == ' ') *c = '_';
+}
+
+static bool tune_cache_find(const char *path, const char *key, md_batch_tuning *t)
+{
+    if (!path) return false;
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char k[256];
+    int chunk, grid, nt;
+    double occ;
+    float ms;
+    bool found = false;
+    while (fscanf(f, "%255s %d %d %d %lf %f", k, &chunk, &grid, &nt, &occ, &ms) == 6) {
+        if (strcmp(k, key) == 0 && chunk >= 1 && chunk <= 64 && (grid == 100 || grid == 50) &&
+            (nt == 4 || nt == NTEST) && occ >= 0.0) {
+            t->chunk = chunk;
+            t->grid_pct = grid;
+            t->test_width = nt;
+            t->half_min_occ = occ;
+            t->ms = ms;
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+static void tune_cache_store(const char *path, const char *key, const md_batch_tuning *t)
+{
+    if (!path) return;
+    std::vector<std::string> keep;
+    if (FILE *f = fopen(path, "r")) {
+        char line[512];
+        while (fgets(line, sizeof line, f)) {
+            char k[256];
+            if (sscanf(line, "%255s", k) == 1 && strcmp(k, key) != 0) keep.push_back(line);
+        }
+        fclose(f);
+    }
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    for (const std::string &l : keep) fputs(l.c_str(), f);
+    fprintf(f, "%s %d %d %d %.6g %.6g\n", key, t->chunk, t->grid_pct, t->test_width, t->half_min_occ, t->ms);
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+// Mean of 3 batched force evaluations with the current tiles (after one
+// untimed one), in ms.
+static md_status time_forces(md_batch *b, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, float *ms)
+{
+    md_status r = batch_force(b, st);
+    if (r != MD_OK) return r;
+    cudaEventRecord(e0, st);
+    for (int rep = 0; rep < 3 && r == MD_OK; rep++) r = batch_force(b, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    *ms = t / 3.f;
+    return r;
+}
+
+md_status md_batch_tune_tiles(md_batch *b, void *cuda_stream, const char *cache_path, md_batch_tuning *out)
+{
+    if (!b || !out) return MD_ERR_ARG;
     if (!b->has_mol) return MD_ERR_STATE;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const int chunks[] = {1, 2, 4, 8, 16};
-    const int grids[] = {100, 50};
+    md_batch_tuning t;
+    memset(&t, 0, sizeof t);
+    tune_key(b, t.key, sizeof t.key);
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0), "event");
     BCK(cudaEventCreate(&e1), "event");
-    float best = 1e30f;
-    int bc = b->chunk, bg = b->grid_frac_pct;
-    md_status ms = batch_force(b, st);  // warm-up
-    for (int gi = 0; gi < 2 && ms == MD_OK; gi++)
-        for (int ci = 0; ci < 5 && ms == MD_OK; ci++) {
-            b->chunk = chunks[ci];
-            b->grid_frac_pct = grids[gi];
-            cudaEventRecord(e0, st);
-            for (int rep = 0; rep < 3 && ms == MD_OK; rep++) ms = batch_force(b, st);
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            float t = 0.f;
-            cudaEventElapsedTime(&t, e0, e1);
-            t /= 3.f;
-            if (t < best) {
-                best = t;
-                bc = chunks[ci];
-                bg = grids[gi];
-            }
+    auto apply = [&](int chunk, int grid, int nt, double occ) -> md_status {
+        b->chunk = chunk;
+        b->grid_frac_pct = grid;
+        b->test_width = nt;
+        if (occ != b->half_min_occ) {
+            b->half_min_occ = occ;
+            return apply_shell_policy(b, st);
         }
+        return MD_OK;
+    };
+    // the defaults, timed for the comparison
+    md_status ms = apply(2, 100, NTEST, 0.0);
+    if (ms == MD_OK) ms = time_forces(b, st, e0, e1, &t.default_ms);
+    md_batch_tuning cached = t;
+    if (ms == MD_OK && tune_cache_find(cache_path, t.key, &cached)) {
+        t = cached;
+        t.from_cache = 1;
+        ms = apply(t.chunk, t.grid_pct, t.test_width, t.half_min_occ);
+    } else if (ms == MD_OK) {
+        const int chunks[] = {1, 2, 4, 8};
+        const int grids[] = {100, 50};
+        const int widths[] = {4, NTEST};
+        const double occs[] = {0.0, 2.0, 6.0};
+        float best = 1e30f;
+        for (double occ : occs)
+            for (int nt : widths)
+                for (int grid : grids)
+                    for (int chunk : chunks) {
+                        if (ms != MD_OK) break;
+                        float tm = 0.f;
+                        ms = apply(chunk, grid, nt, occ);
+                        if (ms == MD_OK) ms = time_forces(b, st, e0, e1, &tm);
+                        if (ms == MD_OK && tm < best) {
+                            best = tm;
+                            t.chunk = chunk;
+                            t.grid_pct = grid;
+                            t.test_width = nt;
+                            t.half_min_occ = occ;
+                            t.ms = tm;
+                        }
+                    }
+        if (ms == MD_OK) ms = apply(t.chunk, t.grid_pct, t.test_width, t.half_min_occ);
+        if (ms == MD_OK) tune_cache_store(cache_path, t.key, &t);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->chunk = bc;
-    b->grid_frac_pct = bg;
     drop_graphs(b);
-    if (best_chunk) *best_chunk = bc;
-    if (best_grid_pct) *best_grid_pct = bg;
-    if (best_ms) *best_ms = best;
+    b->forces_valid = false;
+    *out = t;
     return ms;
+}
+
+md_status md_batch_tune(md_batch *b, void *cuda_stream, int32_t *best_chunk, int32_t *best_grid_pct, float *best_ms)
+{
+    md_batch_tuning t;
+    md_status ms = md_batch_tune_tiles(b, cuda_stream, nullptr, &t);
+    if (ms != MD_OK) return ms;
+    if (best_chunk) *best_chunk = t.chunk;
+    if (best_grid_pct) *best_grid_pct = t.grid_pct;
+    if (best_ms) *best_ms = t.ms;
+    return MD_OK;
 }
 
 }  // extern "C"

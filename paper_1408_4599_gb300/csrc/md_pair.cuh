@@ -710,7 +710,9 @@ __device__ __forceinline__ void for_each_cell(long long ncell, int parts, unsign
 // a lane meets one i for many consecutive pairs (sbase = storage slot of
 // the pass's first i).  chunk_end is then not called.
 // cell_start holds global slots; c is the cell index inside the grid.
-template <class SIG, bool HALF, int M = 1, class Op, class Tile>
+// NT: candidates per lane per test round of the chunked pipeline (a tile
+// parameter of the batched replicas' autotuner; <= NTEST).
+template <class SIG, bool HALF, int M = 1, int NT = NTEST, class Op, class Tile>
 __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView &g, const int *__restrict__ cell_start,
                                               const float4 *__restrict__ com, const float4 *__restrict__ geo,
                                               const double *__restrict__ r64, int K, long long c, Tile &T,
@@ -1034,13 +1036,14 @@ __device__ __forceinline__ void traverse_cell(const DevModel &m, const GridView 
                     };
                     {
                         // warp-uniform: half-width rounds when the i's candidates fit
-                        if (nj - skip_to <= 32 * (NTEST / 2)) {
+                        static_assert(NT <= NTEST && NT % 2 == 0, "test rounds of 2 ... NTEST candidates per lane");
+                        if (nj - skip_to <= 32 * (NT / 2)) {
                             make_room();
-                            round(std::integral_constant<int, NTEST / 2>{}, skip_to);
+                            round(std::integral_constant<int, NT / 2>{}, skip_to);
                         } else {
-                            for (int kb = skip_to; kb < nj; kb += 32 * NTEST) {
+                            for (int kb = skip_to; kb < nj; kb += 32 * NT) {
                                 make_room();
-                                round(std::integral_constant<int, NTEST>{}, kb);
+                                round(std::integral_constant<int, NT>{}, kb);
                             }
                         }
                     }

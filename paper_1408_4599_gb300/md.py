@@ -54,6 +54,17 @@ class md_observables(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class md_batch_tuning(C.Structure):
+    _fields_ = [("chunk", C.c_int32), ("grid_pct", C.c_int32), ("test_width", C.c_int32),
+                ("half_min_occ", C.c_double), ("ms", C.c_float), ("default_ms", C.c_float),
+                ("from_cache", C.c_int32), ("key", C.c_char * 160)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["key"] = self.key.decode()
+        return d
+
+
 class md_kernel_times(C.Structure):
     _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8)]
 
@@ -70,7 +81,7 @@ EXPORTS = ("md_create", "md_set_molecules", "md_compute_forces", "md_step", "md_
            "md_param_grad", "md_batch_create", "md_batch_set_molecules", "md_batch_compute_forces", "md_batch_step",
            "md_batch_energy_virial", "md_batch_get_molecules", "md_batch_get_forces", "md_batch_tune",
            "md_batch_destroy", "md_batch_last_error", "md_batch_set_thermostat", "md_kinetic_noalloc",
-           "md_fp32_peak")
+           "md_fp32_peak", "md_batch_tune_tiles")
 
 
 def lib():
@@ -109,13 +120,14 @@ def lib():
         L.md_batch_get_forces.argtypes = [vp, vp, vp, i32, vp]
         L.md_batch_tune.argtypes = [vp, vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_float)]
         L.md_batch_set_thermostat.argtypes = [vp, dp, vp]
+        L.md_batch_tune_tiles.argtypes = [vp, vp, C.c_char_p, C.POINTER(md_batch_tuning)]
         L.md_batch_destroy.argtypes = [vp]
         L.md_batch_destroy.restype = None
         L.md_batch_last_error.argtypes = [vp]
         L.md_batch_last_error.restype = C.c_char_p
         for name in ("md_batch_create", "md_batch_set_molecules", "md_batch_compute_forces", "md_batch_step",
                      "md_batch_energy_virial", "md_batch_get_molecules", "md_batch_get_forces", "md_batch_tune",
-                     "md_batch_set_thermostat"):
+                     "md_batch_set_thermostat", "md_batch_tune_tiles"):
             getattr(L, name).restype = C.c_int
         L.md_kinetic_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, C.c_double, dp, C.c_double, vp, vp]
         L.md_kinetic_noalloc.restype = C.c_int
@@ -532,6 +544,14 @@ class Batch:
         bc, bg, bm = C.c_int32(), C.c_int32(), C.c_float()
         _bcheck(lib().md_batch_tune(self.h, _stream_ptr(stream), C.byref(bc), C.byref(bg), C.byref(bm)), self.h)
         return {"chunk": bc.value, "grid_pct": bg.value, "force_ms": bm.value}
+
+    def tune_tiles(self, cache_path=None, stream=None):
+        """Tile autotuner (md_batch_tune_tiles); cache_path: optional text
+        file of earlier choices.  Returns the md_batch_tuning as a dict."""
+        t = md_batch_tuning()
+        p = cache_path.encode() if cache_path else None
+        _bcheck(lib().md_batch_tune_tiles(self.h, _stream_ptr(stream), p, C.byref(t)), self.h)
+        return t.as_dict()
 
     def close(self):
         if self.h:

@@ -215,3 +215,37 @@ def test_full_size_batch_sampled_parity():
         Fo, to, oo = oracle.forces(c["model"], s, c["r"], c["q"], use_cells=True)
         ncs = [int(math.floor(L / (c["rc"] * (1 + 1e-9)))) for L in c["box"]]
         check_parity(f"batch512/{c['name']}", c, Fs[k], ts[k], obs[k], Fo, to, oo, exact_examined=min(ncs) >= 3)
+
+
+def test_tile_tuner_choices_cache_and_results(tmp_path):
+    """md_batch_tune_tiles on a dilute and a dense replica set: the chosen
+    tiles are among the candidates and no slower than the defaults (which
+    are candidates), the forces with the chosen tiles agree with the
+    defaults' within the parity tolerance (the tiles change only the
+    summation order and the stencil form), the two sets fall in different
+    occupancy buckets of the cache key, and a second call takes the cached
+    choice without timing."""
+    cache = str(tmp_path / "tune.txt")
+    keys = set()
+    for name, rho in (("dilute", 0.06), ("dense", 0.7)):
+        cfgs = [mdgen.config_replica(k, 1500 + 400 * k, rho, 1.0) for k in range(6)]
+        b = md.Batch(cfgs, half_shell=1).set()
+        b.compute_forces()
+        F0, t0 = b.forces()
+        t = b.tune_tiles(cache)
+        assert t["from_cache"] == 0
+        assert t["chunk"] in (1, 2, 4, 8) and t["grid_pct"] in (100, 50) and t["test_width"] in (4, 8)
+        assert t["half_min_occ"] in (0.0, 2.0, 6.0)
+        assert t["ms"] <= 1.15 * t["default_ms"], t
+        b.compute_forces()
+        F1, t1 = b.forces()
+        ef, et = rel_err(F1, F0), rel_err(t1, t0)
+        assert np.median(ef) <= 1e-5 and ef.max() <= 1e-3
+        assert np.median(et) <= 1e-5 and et.max() <= 1e-3
+        t2 = b.tune_tiles(cache)
+        assert t2["from_cache"] == 1 and t2["key"] == t["key"]
+        assert (t2["chunk"], t2["grid_pct"], t2["test_width"], t2["half_min_occ"]) == \
+            (t["chunk"], t["grid_pct"], t["test_width"], t["half_min_occ"])
+        keys.add(t["key"])
+        b.close()
+    assert len(keys) == 2
