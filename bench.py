@@ -396,11 +396,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": ("f32 site math; per-molecule force/torque in f32 (half shell: per-lane run sums and f32 "
-                      "vector reductions into per-molecule records); energy/virial f32 pass sums into f64; "
-                      "f64 state and integrator") if half else
-                     ("f32 site math; per-molecule force/torque: f32 warp sums of <= 32 pair terms into f64; "
-                      "energy/virial f32 pass sums into f64; f64 state and integrator"),
+            "dtype": dtype_label(("half" if args.cell_div == 1 else "records") if half else "full"),
             "data": "synthetic (seeded 2CLJQ fluid, random orientations with close site contacts relieved)",
             "config": {"workload": WORKLOAD_2CLJQ,
                        "shell": args.shell, "cells_per_cutoff": args.cell_div,
@@ -571,7 +567,8 @@ def run_single(args, md, torch, dev, rank):
     achieved = fpp * o["n_mol_pairs"] / (f_ms / 1e3) / 1e12
     line = {"metric": METRIC, "value": o["n_site_pairs"] * steps / t, "unit": UNIT, "n_gpus": 1, "steps": steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 site math, f64 accumulation/state", "data": "synthetic (seeded)",
+            "vs_baseline": None, "dtype": dtype_label("half" if args.cell_div == 1 else "records"),
+            "data": "synthetic (seeded)",
             "config": {"workload": what, "shell": "half", "cells_per_cutoff": args.cell_div,
                        "l2": "working set > L2" if flush is None else "flushed (512 MB write) before every timed step"},
             "molecule_updates_per_s": None if evals_only else n * steps / t,
@@ -584,6 +581,17 @@ def run_single(args, md, torch, dev, rank):
     if graph is not None:
         line["graph_replay"] = graph
     return line
+
+
+def dtype_label(kind):
+    """The arithmetic the force path computes in: "half" (run-drained half
+    shell), "full" (deterministic full shell) or "records" (per-pair
+    reductions into FP32 per-molecule records: the batched launch and the
+    chunked half shell)."""
+    acc = {"half": "per-molecule force/torque in f32 records (per-lane run sums, f32 vector reductions)",
+           "full": "per-molecule force/torque totals in f64",
+           "records": "per-molecule force/torque in f32 records (f32 vector reductions per pair)"}[kind]
+    return f"f32 site math; {acc}; energy/virial f32 lane sums flushed to f64 every 256 terms; f64 state and integrator"
 
 
 def timed_calls(fn, steps, stream, torch, flush=None):
@@ -635,7 +643,7 @@ def run_sweep(args, md, torch, dev, rank):
     line = {"metric": METRIC, "value": big["n"] / (big["ms_per_step"] / 1e3), "unit": "molecule updates/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": big["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 site math, f64 accumulation/state", "data": "synthetic (seeded)",
+            "dtype": dtype_label("half" if args.cell_div == 1 else "records"), "data": "synthetic (seeded)",
             "config": {"workload": "LJTS fluid rho=0.6 T=0.95 rc=2.5 size sweep (one md step each)", "shell": "half",
                        "cells_per_cutoff": args.cell_div,
                        "l2": "flushed (512 MB write) before every timed md_step(1); graph_replay_ms_per_step: one "
@@ -708,7 +716,7 @@ def run_batch(args, md, torch, dev, rank):
     value = pairs_step * args.steps / t_batch
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t_batch / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 site math, f64 accumulation/state", "data": "synthetic (seeded)",
+            "vs_baseline": None, "dtype": dtype_label("records"), "data": "synthetic (seeded)",
             "config": {"workload": f"{len(cfgs)} 2CLJQ+dipole replicas, N log-uniform [500,20000] (sum {n_tot}), "
                                    "rho U(0.05,0.75), rc=3, eps_RF=inf, one batched NVT md step (velocity rescaling "
                                    "to each replica's T, CUDA graph), after an untimed relaxation",
