@@ -674,7 +674,7 @@ md_status md_create(const double box[3], double cutoff, const md_site_types *typ
     // cell being split into up to 4 units in small systems
     long long fb = (4 * ncell + MD_WARPS - 1) / MD_WARPS;
     s->n_force_blocks = (int)(fb < force_blocks_default() ? fb : force_blocks_default());
-    s->n_kin_blocks = 152 * 4;
+    s->n_kin_blocks = device_sms() * 4;
     DevState &d = s->d;
     cudaError_t e = cudaMalloc((void **)&d.cell_count, sizeof(int) * ncell);
     if (e == cudaSuccess) e = cudaMalloc((void **)&d.cell_start, sizeof(int) * (ncell + 1));

@@ -39,7 +39,21 @@ __global__ void k_force_finalize(const float *acc, long long n, double *F, doubl
 
 }  // namespace
 
-int force_blocks_default() { return 152 * 16; }
+// SMs of the current device (152 on GB300 if the query fails)
+int device_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        return 152;
+    }
+    return sms;
+}
+
+// upper bound of the force grid: 16 blocks per SM (the kernels' occupancy
+// is lower; the launch trims the grid to what is resident)
+int force_blocks_default() { return device_sms() * 16; }
 
 cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half_shell, int dynamic_cells, int n_blocks,
                          cudaStream_t s)

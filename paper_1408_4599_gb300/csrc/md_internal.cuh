@@ -133,6 +133,7 @@ cudaError_t launch_scatter_out(const DevState &d, const double *src, int width, 
 cudaError_t launch_gather_in(DevState &d, const double *src, int width, double *dst, cudaStream_t s);
 cudaError_t launch_prepare_input(const Grid &g, DevState &d, cudaStream_t s);
 int force_blocks_default();
+int device_sms();
 cudaError_t launch_force_finalize(DevState &d, cudaStream_t s);
 int adjoint_nacc(const DevModel &m);
 cudaError_t launch_adjoint(const Grid &g, const DevModel &m, const DevState &d, int half_shell, int dynamic_cells,
