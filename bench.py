@@ -284,7 +284,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-drift", action="store_true", help="default run: skip the 1000-step NVE drift leg")
     ap.add_argument("--no-secondary", action="store_true",
-                    help="default run: skip the compact secondary workloads (LJ N=4096, slab, replicas, adjoint)")
+                    help="default run: skip the compact secondary workloads "
+                         "(LJ N=4096, slab, replicas, adjoint, size sweep)")
     ap.add_argument("--workload", default="2cljq",
                     choices=["2cljq", "batch", "adjoint", "lj", "slab", "lj200m", "sweep"],
                     help="2cljq: the headline step; batch: 512 uneven replicas; adjoint: parameter gradients; "
@@ -433,9 +434,11 @@ def secondary(args, md, torch, dev):
     beside the headline (each its own seeded input, CUDA-event timing):
     the LJTS fluid N = 4096 (md_step, single calls and graph replay), the
     LJTS vapour-liquid slab N = 4,194,304, the 512 batched replicas against
-    the same replicas as separate systems, and the adjoint (parameter
+    the same replicas as separate systems, the adjoint (parameter
     gradients) against the forward force kernel on the same 4-site
-    configurations.  A failure in one is recorded in place of its numbers."""
+    configurations, and the cost of an LJTS md step against N = 4096 ...
+    16,777,216 (the O(N) sweep).  A failure in one is recorded in place of
+    its numbers."""
     import copy
     out = {}
 
@@ -445,7 +448,8 @@ def secondary(args, md, torch, dev):
         for k, v in kw.items():
             setattr(a, k, v)
         t0 = time.perf_counter()
-        fn = {"batch": run_batch, "adjoint": run_adjoint, "lj": run_single, "slab": run_single}[workload]
+        fn = {"batch": run_batch, "adjoint": run_adjoint, "lj": run_single, "slab": run_single,
+              "sweep": run_sweep}[workload]
         line = fn(a, md, torch, dev, 0)
         line["wall_s"] = time.perf_counter() - t0
         return line
@@ -463,7 +467,8 @@ def secondary(args, md, torch, dev):
               "wall_s")),
             ("adjoint_4site_50000", "adjoint", {"steps": 4, "configs": 2},
              ("adjoint_kernel_ms_per_config", "forward_force_kernel_ms_per_config", "adjoint_ms_per_ensemble",
-              "forward_ms_per_ensemble", "config", "wall_s"))):
+              "forward_ms_per_ensemble", "config", "wall_s")),
+            ("lj_size_sweep", "sweep", {"steps": 5}, ("sweep", "wall_s"))):
         try:
             line = sub(workload, **kw)
             d = keep(line, keys)
