@@ -51,7 +51,10 @@ struct ForceOp {
     // the half shell is drained in runs (drain): a lane keeps its i's force
     // and torque in registers over consecutive pairs of that i
     static constexpr bool RUNS = HALF && RUNS_;
-    using Tile = std::conditional_t<RUNS, WarpTileD<ForceExtraHalf, QRUN>, WarpTile<ForceExtra, QCAP>>;
+    // linear molecules stage the candidates' axes with their COMs (the
+    // drained pairs then read no global memory)
+    using Tile = std::conditional_t<RUNS, WarpTileD<ForceExtraHalf, QRUN, SIG::LIN && !SIG::DYN>,
+                                    WarpTile<ForceExtra, QCAP>>;
     const DevModel &m;
     const ForceArgs &A;
     int K;
@@ -186,7 +189,7 @@ struct ForceOp {
     __device__ __forceinline__ void run_step(Tile &Tl, Run &r, int e, int sbase, Exact &exact, float band_lo)
     {
         const int q = Tl.queue[e];
-        const int il = q >> 16, k = q & 0xffff;
+        const int il = q >> Tile::QSHIFT, k = q & ((1 << Tile::QSHIFT) - 1);
         if (il != r.cur) {
             if (r.cur >= 0) flush_i(sbase + r.cur, r.a);
             r.cur = il;
@@ -201,7 +204,10 @@ struct ForceOp {
         const float X0 = r.I.c.x - cj.x, X1 = r.I.c.y - cj.y, X2 = r.I.c.z - cj.z;
         const int js = Tl.cand_slot(k);
         float Fp[3], tp[3], tq[3], Up;
-        mol_pair<SIG, true>(m, X0, X1, X2, r.I, A.geo + (long long)js * K, Fp, tp, tq, Up);
+        if constexpr (Tile::AXES)
+            mol_pair<SIG, true, true>(m, X0, X1, X2, r.I, nullptr, Fp, tp, tq, Up, Tl.axis(k));
+        else
+            mol_pair<SIG, true>(m, X0, X1, X2, r.I, A.geo + (long long)js * K, Fp, tp, tq, Up);
         // queued inside the FP32 band around r_c^2: the FP64 test decides
         // (after the pair terms, so that no branch holds back their loads;
         // a pair outside the cut-off is dropped)
