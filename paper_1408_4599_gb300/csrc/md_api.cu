@@ -45,6 +45,7 @@ struct md_system {
     DevState d;
     md_options opt;
     int half_eff;                // half shell actually used (needs >= 3 cells per axis)
+    bool acc_zeroed = false;     // the last rebuild cleared the FP32 accumulator records
     int n_force_blocks, n_kin_blocks;
     long long cap;               // allocated molecules
     bool has_mol, binned, forces_valid;
@@ -535,8 +536,9 @@ md_status do_rebuild(md_system *s, cudaStream_t st, bool need_cellid, const doub
 {
     TimeScope ts(s, st, 1);
     if (need_cellid) CK(launch_cellid(s->g, s->d, st), "cell id kernel");
-    CK(launch_rebuild(s->g, s->m, s->d, st, beta, s->opt.deterministic), "cell rebuild kernels");
+    CK(launch_rebuild(s->g, s->m, s->d, st, beta, s->opt.deterministic, s->half_eff), "cell rebuild kernels");
     s->binned = true;
+    s->acc_zeroed = s->half_eff && !s->opt.deterministic && s->d.n > 0;
     return MD_OK;
 }
 
@@ -544,7 +546,9 @@ md_status do_force(md_system *s, cudaStream_t st)
 {
     TimeScope ts(s, st, 3);
     // cells in counter order unless the energy sums must group identically on every launch
-    CK(launch_force(s->g, s->m, s->d, s->half_eff, !s->opt.deterministic, s->n_force_blocks, st), "force kernel");
+    CK(launch_force(s->g, s->m, s->d, s->half_eff, !s->opt.deterministic, s->n_force_blocks, st, s->acc_zeroed),
+       "force kernel");
+    s->acc_zeroed = false;
     s->forces_valid = true;
     s->f_in_acc = s->half_eff != 0;
     return MD_OK;
@@ -759,9 +763,9 @@ md_status md_set_molecules(md_system *s, int64_t n, const int32_t *comp_id, cons
     ms = do_rebuild(s, st, true);
     if (ms != MD_OK) return ms;
     if (!on_device) {
+        int bad = 0;  // read on the stream: one wait for the copies, the kernels and the flag
+        CK(cudaMemcpyAsync(&bad, d.flags + FLAG_INPUT, sizeof bad, cudaMemcpyDeviceToHost, st), "reading the input flag");
         CK(cudaStreamSynchronize(st), "md_set_molecules sync");
-        int bad = 0;
-        CK(cudaMemcpy(&bad, d.flags + FLAG_INPUT, sizeof bad, cudaMemcpyDeviceToHost), "reading the input flag");
         if (bad) {
             CK(cudaMemset(d.flags + FLAG_INPUT, 0, sizeof(int)), "clear input flag");
             s->has_mol = false;
@@ -934,17 +938,20 @@ md_status md_get_molecules(md_system *s, double *r, double *v, double *q, double
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     DevState &d = s->d;
-    const double *src[4] = {d.r, d.v, d.q, d.j};
     double *dst[4] = {r, v, q, j};
     double *tmp[4] = {d.r2, d.v2, d.q2, d.j2};
     const int w[4] = {3, 3, 4, 3};
-    for (int k = 0; k < 4; k++) {
-        if (!dst[k] || d.n == 0) continue;
-        double *target = on_device ? dst[k] : tmp[k];
-        CK(launch_scatter_out(d, src[k], w[k], target, st), "scatter kernel");
+    double *target[4];
+    for (int k = 0; k < 4; k++) target[k] = !dst[k] ? nullptr : (on_device ? dst[k] : tmp[k]);
+    if (d.n > 0) {
+        // one kernel for the four arrays, then the copies back to back
+        CK(launch_scatter_state(d, target[0], target[1], target[2], target[3], st), "scatter kernel");
         if (!on_device)
-            CK(cudaMemcpyAsync(dst[k], tmp[k], sizeof(double) * w[k] * (size_t)d.n, cudaMemcpyDeviceToHost, st),
-               "copy state to host");
+            for (int k = 0; k < 4; k++)
+                if (dst[k])
+                    CK(cudaMemcpyAsync(dst[k], tmp[k], sizeof(double) * w[k] * (size_t)d.n, cudaMemcpyDeviceToHost,
+                                       st),
+                       "copy state to host");
     }
     CK(cudaStreamSynchronize(st), "md_get_molecules sync");
     return check_flags(s);

@@ -28,15 +28,22 @@ __global__ void k_prepare(Grid g, double *r, double *q, const double *v, const d
     for (int k = 0; k < 3; k++) {
         double x = r[3 * s + k];
         bad |= !isfinite(x);
-        x -= g.L[k] * floor(x / g.L[k]);
-        if (x >= g.L[k]) x -= g.L[k];
-        if (x < 0.0) x = 0.0;
-        r[3 * s + k] = x;
+        // 0 <= x < L as one unsigned compare of the bit patterns (negative
+        // values and NaN compare above); only a position outside the box
+        // pays the FP64 division of the wrap
+        if ((unsigned long long)__double_as_longlong(x) >= (unsigned long long)__double_as_longlong(g.L[k])) {
+            x -= g.L[k] * floor(x / g.L[k]);
+            if (x >= g.L[k]) x -= g.L[k];
+            if (x < 0.0) x = 0.0;
+            r[3 * s + k] = x;
+        }
     }
     double w = q[4 * s], a = q[4 * s + 1], b = q[4 * s + 2], c = q[4 * s + 3];
-    double nn = sqrt(w * w + a * a + b * b + c * c);
-    bad |= !(nn > 0.0) || !isfinite(nn);
-    double inv = 1.0 / nn;
+    const double nn2 = w * w + a * a + b * b + c * c, e = nn2 - 1.0;
+    bad |= !(nn2 > 0.0) || !isfinite(nn2);
+    // |q|^-1 = (1 + e)^(-1/2): the cubic series is exact to FP64 rounding for
+    // |e| < 1e-4 (unit quaternions as given), 1/sqrt otherwise
+    const double inv = fabs(e) < 1e-4 ? 1.0 + e * (-0.5 + e * (0.375 - 0.3125 * e)) : 1.0 / sqrt(nn2);
     q[4 * s] = w * inv;
     q[4 * s + 1] = a * inv;
     q[4 * s + 2] = b * inv;
@@ -264,7 +271,9 @@ __global__ void k_reorder_pack(Grid g, DevModel m, DevState d, const double *bet
 // zero for the next step) and writes its whole record there.  The reads
 // are in storage order; the writes land near s, since molecules rarely
 // change cell in one step.
-template <bool BETA>  // BETA: apply the velocity-rescaling factor (NVT steps)
+// ZACC: also clear the slot's FP32 accumulator record (half shell), so the
+// force kernel that follows needs no separate clearing pass.
+template <bool BETA, bool ZACC>  // BETA: apply the velocity-rescaling factor (NVT steps)
 __global__ void k_scatter_pack(Grid g, DevModel m, DevState d, const double *beta)
 {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -291,7 +300,33 @@ __global__ void k_scatter_pack(Grid g, DevModel m, DevState d, const double *bet
     reinterpret_cast<double2 *>(d.q2)[2 * p] = q01;
     reinterpret_cast<double2 *>(d.q2)[2 * p + 1] = q23;
     d.ids2[p] = d.ids[s];
+    if constexpr (ZACC) {
+        float4 *a = reinterpret_cast<float4 *>(d.facc) + 2 * p;
+        a[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        a[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     pack_one(g, m, d, p, c, rx, ry, rz, q01.x, q01.y, q23.x, q23.y);
+}
+
+// The four state arrays back in the caller's molecule order (a NULL target
+// is skipped), one thread per molecule.
+__global__ void k_scatter_state(const int *ids, const double *r, const double *v, const double *q, const double *j,
+                                double *dr, double *dv, double *dq, double *dj, long long n)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const long long o = ids[s];
+    if (dr)
+        for (int k = 0; k < 3; k++) dr[3 * o + k] = r[3 * s + k];
+    if (dv)
+        for (int k = 0; k < 3; k++) dv[3 * o + k] = v[3 * s + k];
+    if (dq) {
+        const double2 a = reinterpret_cast<const double2 *>(q)[2 * s], b = reinterpret_cast<const double2 *>(q)[2 * s + 1];
+        reinterpret_cast<double2 *>(dq)[2 * o] = a;
+        reinterpret_cast<double2 *>(dq)[2 * o + 1] = b;
+    }
+    if (dj)
+        for (int k = 0; k < 3; k++) dj[3 * o + k] = j[3 * s + k];
 }
 
 __global__ void k_scatter_out(const int *ids, const double *src, int width, double *dst, long long n)
@@ -370,7 +405,7 @@ void swap_state(DevState &d)
 // down and writes the records itself (no in-cell sort, no separate
 // reorder), leaving cell_count at zero.
 cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaStream_t s, const double *beta,
-                           int deterministic)
+                           int deterministic, int zero_acc)
 {
     cudaError_t e = cudaSuccess;
     if (deterministic) {
@@ -380,8 +415,14 @@ cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaSt
     } else {
         launch_scan(g.ncell, d, s);
         if (d.n > 0) {
-            if (beta) k_scatter_pack<true><<<nblk(d.n, 256), 256, 0, s>>>(g, m, d, beta);
-            else k_scatter_pack<false><<<nblk(d.n, 256), 256, 0, s>>>(g, m, d, beta);
+            const unsigned nb = nblk(d.n, 256);
+            if (beta) {
+                if (zero_acc) k_scatter_pack<true, true><<<nb, 256, 0, s>>>(g, m, d, beta);
+                else k_scatter_pack<true, false><<<nb, 256, 0, s>>>(g, m, d, beta);
+            } else {
+                if (zero_acc) k_scatter_pack<false, true><<<nb, 256, 0, s>>>(g, m, d, beta);
+                else k_scatter_pack<false, false><<<nb, 256, 0, s>>>(g, m, d, beta);
+            }
         }
     }
     e = cudaGetLastError();
@@ -393,6 +434,13 @@ cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaSt
     t = d.j; d.j = d.j2; d.j2 = t;
     int *ti = d.ids; d.ids = d.ids2; d.ids2 = ti;
     return cudaSuccess;
+}
+
+cudaError_t launch_scatter_state(const DevState &d, double *r, double *v, double *q, double *j, cudaStream_t s)
+{
+    if (d.n == 0) return cudaSuccess;
+    k_scatter_state<<<nblk(d.n, 256), 256, 0, s>>>(d.ids, d.r, d.v, d.q, d.j, r, v, q, j, d.n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_scatter_out(const DevState &d, const double *src, int width, double *dst, cudaStream_t s)

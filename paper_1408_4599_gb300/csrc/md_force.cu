@@ -56,7 +56,7 @@ int device_sms()
 int force_blocks_default() { return device_sms() * 16; }
 
 cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half_shell, int dynamic_cells, int n_blocks,
-                         cudaStream_t s)
+                         cudaStream_t s, int acc_zeroed)
 {
     ForceArgs A;
     A.g = g;
@@ -77,7 +77,7 @@ cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half
     // 0; the counter slot after the partials is cleared with them
     cudaError_t e = cudaMemsetAsync(d.partials, 0, sizeof(double) * (P_COUNT * (size_t)n_blocks + 1), s);
     if (e != cudaSuccess) return e;
-    if (half_shell) {
+    if (half_shell && !acc_zeroed) {
         e = cudaMemsetAsync(d.facc, 0, sizeof(float) * FACC_STRIDE * (d.n > 0 ? d.n : 1), s);
         if (e != cudaSuccess) return e;
     }

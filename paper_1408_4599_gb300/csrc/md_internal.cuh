@@ -111,14 +111,17 @@ enum { FLAG_NONFINITE = 0, FLAG_OVERFLOW = 1, FLAG_TIMEOUT = 2, FLAG_INPUT = 3 }
 // (all return cudaGetLastError() of the launch)
 cudaError_t launch_cellid(const Grid &g, DevState &d, cudaStream_t s);
 // beta (device scalar, may be NULL): factor applied to v and j while they are reordered
+// zero_acc (non-deterministic rebuilds): also clear the FP32 accumulator
+// records of the new order, for the half-shell force kernel that follows
 cudaError_t launch_rebuild(const Grid &g, const DevModel &m, DevState &d, cudaStream_t s,
-                           const double *beta = nullptr, int deterministic = 1);
+                           const double *beta = nullptr, int deterministic = 1, int zero_acc = 0);
 cudaError_t launch_sort(long long ncell, DevState &d, cudaStream_t s);
 void swap_state(DevState &d);
 // half shell: the results stay in the FP32 accumulators d.facc until
 // launch_force_finalize; full shell: FP64 d.F, d.tau directly.
+// acc_zeroed: the records are already clear (the rebuild cleared them)
 cudaError_t launch_force(const Grid &g, const DevModel &m, DevState &d, int half_shell, int dynamic_cells, int n_blocks,
-                         cudaStream_t s);
+                         cudaStream_t s, int acc_zeroed = 0);
 // acc32: read the forces from d.facc instead of d.F, d.tau; zero_count:
 // clear the histogram first (not needed after a non-deterministic rebuild,
 // which leaves it at zero)
@@ -129,6 +132,8 @@ cudaError_t launch_rescale(const DevModel &m, DevState &d, double fac_v, double 
 // velocity rescaling to T_target: half-step kinetic energies -> d.thermo[0] = sqrt(T_target / T_half)
 cudaError_t launch_thermostat(const DevModel &m, DevState &d, int n_blocks, double T_target, double dof,
                               cudaStream_t s);
+// r, v, q, j (each may be NULL) in the caller's molecule order, one kernel
+cudaError_t launch_scatter_state(const DevState &d, double *r, double *v, double *q, double *j, cudaStream_t s);
 cudaError_t launch_scatter_out(const DevState &d, const double *src, int width, double *dst, cudaStream_t s);
 cudaError_t launch_gather_in(DevState &d, const double *src, int width, double *dst, cudaStream_t s);
 cudaError_t launch_prepare_input(const Grid &g, DevState &d, cudaStream_t s);
