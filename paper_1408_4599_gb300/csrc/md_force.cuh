@@ -8,16 +8,21 @@
 // GB300 design (CUDA cores -- this is not a dense contraction):
 //   * traversal of md_pair.cuh: one warp per i-cell (cells handed out from
 //     a counter, or by a fixed grid stride in deterministic runs),
-//     candidates staged in shared memory, FP32 cut-off test with an FP64
-//     re-test in a narrow band, hits of consecutive i molecules packed into
-//     32-pair chunks;
-//   * FP32 site-site math (rsqrt/rcp on the MUFU pipe);
-//   * half shell (Newton-3): each pair's terms go straight to the FP32
-//     accumulator records of i and j, two 16-byte vector reductions (F,
-//     tau) per molecule -- faster than per-candidate shared accumulators
-//     for j (a loop over the i's of a chunk, 6 KB of shared memory per warp)
-//     and than a segmented warp sum for i; the records are read directly by
-//     the integrator and converted to FP64 only on demand;
+//     candidates staged in shared memory (with their axes, for linear
+//     molecules in the half shell), FP32 cut-off test of two i molecules
+//     per paired instruction with the FP64 decision in a narrow band;
+//   * FP32 site-site math (rsqrt/rcp on the MUFU pipe, f32x2 where the
+//     math pairs up);
+//   * half shell (Newton-3), cells of edge >= r_c: the hits of a pass
+//     collect in a queue drained in runs, one per lane; a lane keeps its i
+//     molecule's sums in registers while the i stays the same and adds
+//     them to the i's FP32 accumulator record once per run segment, and
+//     adds each pair's reaction to the j record (16-byte vector
+//     reductions); cells of edge >= r_c / 2 and the batched replicas keep
+//     the chunked form (per-pair reductions on both records).  The records
+//     are cleared by the rebuild that precedes the kernel (else by a
+//     memset), read directly by the integrator and converted to FP64 only
+//     on demand;
 //   * full shell: each ordered pair from both sides, a segmented warp sum
 //     per chunk into per-pass i totals in shared memory, plain FP64 stores of
 //     the per-molecule totals, bitwise deterministic;

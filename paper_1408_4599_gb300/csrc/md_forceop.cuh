@@ -55,6 +55,8 @@ struct ForceOp {
     // drained pairs then read no global memory)
     using Tile = std::conditional_t<RUNS, WarpTileD<ForceExtraHalf, QRUN, SIG::LIN && !SIG::DYN>,
                                     WarpTile<ForceExtra, QCAP>>;
+    // four blocks of the run-drained kernel fit an SM's shared memory
+    static_assert(!RUNS || sizeof(Tile) * MD_WARPS <= 55 * 1024, "run-drained tile grew past 4 blocks per SM");
     const DevModel &m;
     const ForceArgs &A;
     int K;
