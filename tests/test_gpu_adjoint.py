@@ -105,8 +105,9 @@ def test_device_configurations_and_parameter_round_trip():
 
 
 def test_autograd_function_backward():
-    """EnsembleUW: forward = ensemble means from the force kernel, backward =
-    the adjoint kernel contracted with the incoming gradient."""
+    """EnsembleUW: forward = the ensemble means of one adjoint pass (equal to
+    the force kernel's observables), backward = that pass's derivatives
+    contracted with the incoming gradient."""
     cfg, r_all, q_all = _ensemble("2cljdq-rf")
     sysm = md.System(cfg)
     theta = torch.tensor(sysm.params(), dtype=torch.float64, requires_grad=True)
@@ -114,7 +115,17 @@ def test_autograd_function_backward():
     loss = 2.0 * out[0] - 0.5 * out[1]
     loss.backward()
     dU, dW, U, W = sysm.param_grad(r_all, q_all)
-    assert out[0].item() == pytest.approx(U, rel=1e-6)
-    assert out[1].item() == pytest.approx(W, rel=1e-5, abs=1e-3)
+    assert out[0].item() == pytest.approx(U, rel=1e-12)
+    assert out[1].item() == pytest.approx(W, rel=1e-12, abs=1e-12)
     assert np.allclose(theta.grad.numpy(), 2.0 * dU - 0.5 * dW, rtol=1e-12, atol=1e-12)
+    # the means agree with the force kernel's observables
+    Uf = Wf = 0.0
+    for c in range(r_all.shape[0]):
+        sysm.set(r_all[c], q_all[c])
+        sysm.compute_forces()
+        o = sysm.observables()
+        Uf += o["U_pot"] + o["U_lrc"]
+        Wf += o["W"] + o["W_lrc"]
+    assert out[0].item() == pytest.approx(Uf / r_all.shape[0], rel=1e-6)
+    assert out[1].item() == pytest.approx(Wf / r_all.shape[0], rel=1e-5, abs=1e-3)
     sysm.close()
