@@ -43,12 +43,14 @@ using namespace mdk;
 // most 128 registers) for models of up to 3 merged sites (the run-drained
 // half shell keeps its i molecule and i sums in registers across the run and
 // spills under the 102-register cap of 5 blocks; 3 blocks measured 8% slower
-// on the 2CLJQ fluid); 3 (168) for the larger compiled signatures, whose
+// on the 2CLJQ fluid); 5 for single-site LJ in the half shell (96 registers
+// without spills, and its compact tile fits five blocks' shared memory:
+// 2.5-5% faster than 4); 3 (168) for the larger compiled signatures, whose
 // site loops spill at 128 registers; 2 for the run-time signature.
 template <class SIG, bool HALF>
 constexpr int force_min_blocks()
 {
-    return SIG::DYN ? 2 : (SIG::S > 3 ? 3 : 4);
+    return SIG::DYN ? 2 : (SIG::S > 3 ? 3 : (SIG::SINGLE && HALF ? 5 : 4));
 }
 
 // Dynamic shared memory of one block: the warps' tiles, then (M = 2) their

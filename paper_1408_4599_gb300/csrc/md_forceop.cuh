@@ -52,8 +52,9 @@ struct ForceOp {
     // and torque in registers over consecutive pairs of that i
     static constexpr bool RUNS = HALF && RUNS_;
     // linear molecules stage the candidates' axes with their COMs (the
-    // drained pairs then read no global memory)
-    using Tile = std::conditional_t<RUNS, WarpTileD<ForceExtraHalf, QRUN, SIG::LIN && !SIG::DYN>,
+    // drained pairs then read no global memory); linear and single-site
+    // molecules use the compact tile
+    using Tile = std::conditional_t<RUNS, WarpTileD<ForceExtraHalf, QRUN, SIG::LIN && !SIG::DYN, (SIG::LIN || SIG::SINGLE) && !SIG::DYN>,
                                     WarpTile<ForceExtra, QCAP>>;
     // four blocks of the run-drained kernel fit an SM's shared memory
     static_assert(!RUNS || sizeof(Tile) * MD_WARPS <= 55 * 1024, "run-drained tile grew past 4 blocks per SM");

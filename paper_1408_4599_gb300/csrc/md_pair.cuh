@@ -621,20 +621,21 @@ struct WarpTile {
 // (-z, -z), so that one f32x2 instruction advances the tests of two i
 // molecules against it, and 32 far-away sentinels after the window's last
 // candidate, so that test rounds need no range check; queue entries
-// (i << 16) | k.  AX (linear molecules): the candidates' axes are staged
-// beside them, so that the drained pairs read no global memory; to keep
-// four blocks per SM the tile then stores -z once (duplicated in registers
-// by the test) and 16-bit queue entries (i << 8) | k.  (Single-site
-// molecules keep the wider layout: measured 3-4% faster for them.)
-template <class Extra, int QC, bool AX = false>
+// (i << 16) | k.  CP (compact): -z stored once (the test duplicates it in a
+// register pair) and 16-bit queue entries (i << 8) | k.  AX (linear
+// molecules, compact): the candidates' axes staged beside them, so that the
+// drained pairs read no global memory, in less shared memory than the wide
+// layout without axes (four blocks per SM).  Single-site molecules use the
+// compact layout without axes, which lets five blocks fit an SM.
+template <class Extra, int QC, bool AX = false, bool CP = AX>
 struct WarpTileD {
-    static_assert(!AX || JCAP <= 256, "16-bit queue entries hold k in 8 bits");
+    static_assert(!CP || JCAP <= 256, "16-bit queue entries hold k in 8 bits");
     static constexpr int QCAPACITY = QC;
     static constexpr bool DUP = true;
     static constexpr bool AXES = AX;
-    static constexpr int QSHIFT = AX ? 8 : 16;
-    using ZT = std::conditional_t<AX, float, float2>;
-    using QT = std::conditional_t<AX, unsigned short, int>;
+    static constexpr int QSHIFT = CP ? 8 : 16;
+    using ZT = std::conditional_t<CP, float, float2>;
+    using QT = std::conditional_t<CP, unsigned short, int>;
     float4 jd[JCAP + 32];
     ZT jz[JCAP + 32];
     int jslot[JCAP];               // storage slot of each candidate
@@ -651,7 +652,7 @@ struct WarpTileD {
     __device__ __forceinline__ void stage(int t, float x_, float y_, float z_, int js, int o)
     {
         jd[t] = make_float4(-x_, -x_, -y_, -y_);
-        if constexpr (AX) jz[t] = -z_;
+        if constexpr (CP) jz[t] = -z_;
         else jz[t] = make_float2(-z_, -z_);
         jslot[t] = js;
         jst[t] = (unsigned char)o;
@@ -672,7 +673,7 @@ struct WarpTileD {
     __device__ __forceinline__ float4 dxy(int k) const { return jd[k]; }
     __device__ __forceinline__ float2 dz(int k) const
     {
-        if constexpr (AX) {
+        if constexpr (CP) {
             const float z = jz[k];
             return make_float2(z, z);
         } else {
@@ -683,7 +684,7 @@ struct WarpTileD {
     __device__ __forceinline__ void pad(int nj, int lane)
     {
         jd[nj + lane] = make_float4(-1.0e18f, -1.0e18f, -1.0e18f, -1.0e18f);
-        if constexpr (AX) jz[nj + lane] = -1.0e18f;
+        if constexpr (CP) jz[nj + lane] = -1.0e18f;
         else jz[nj + lane] = make_float2(-1.0e18f, -1.0e18f);
     }
 };
