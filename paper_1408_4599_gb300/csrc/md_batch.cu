@@ -158,10 +158,11 @@ __global__ void k_reorder_pack_b(const RepGrid *G, const int *rep, DevModel m, D
     const RepGrid &g = G[rep[s]];
     const int c = d.cell[o] - (int)g.cell0;
     const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
-    d.com[s] = make_float4((float)(rx - (cx + 0.5) * g.ell[0]), (float)(ry - (cy + 0.5) * g.ell[1]),
-                           (float)(rz - (cz + 0.5) * g.ell[2]), 0.f);
+    // conversions on the integer pipe (md_fpconv.cuh), the same bits as the hardware's
+    d.com[s] = make_float4(d2f_bits(rx - int_plus_half(cx) * g.ell[0]), d2f_bits(ry - int_plus_half(cy) * g.ell[1]),
+                           d2f_bits(rz - int_plus_half(cz) * g.ell[2]), 0.f);
     if (m.single_lj_at_com) return;
-    const float w = (float)qw, x = (float)qx, y = (float)qy, z = (float)qz;
+    const float w = d2f_bits(qw), x = d2f_bits(qx), y = d2f_bits(qy), z = d2f_bits(qz);
     const float R[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
                         2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
                         2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};

@@ -10,6 +10,8 @@
 #include <climits>
 
 using mdk::cell_coord;
+using mdk::d2f_bits;
+using mdk::int_plus_half;
 
 namespace {
 
@@ -207,19 +209,21 @@ __global__ void k_sort_cells(const int *start, const int *perm, const int *ids, 
 
 // The FP32 data the force kernel reads for the molecule in slot s of cell
 // c: its centre of mass relative to the cell centre (formed in FP64, then
-// rounded) and the space-frame site offsets and axes R(q) d, R(q) e.
+// rounded) and the space-frame site offsets and axes R(q) d, R(q) e.  The
+// conversions run on the integer pipe (md_fpconv.cuh: the same bits as the
+// hardware's, which would occupy the FP64 pipe).
 __device__ __forceinline__ void pack_one(const Grid &g, const DevModel &m, const DevState &d, long long s, int c,
                                          double rx, double ry, double rz, double qw, double qx, double qy, double qz)
 {
     int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
     float4 cm;
-    cm.x = (float)(rx - (cx + 0.5) * g.ell[0]);
-    cm.y = (float)(ry - (cy + 0.5) * g.ell[1]);
-    cm.z = (float)(rz - (cz + 0.5) * g.ell[2]);
+    cm.x = d2f_bits(rx - int_plus_half(cx) * g.ell[0]);
+    cm.y = d2f_bits(ry - int_plus_half(cy) * g.ell[1]);
+    cm.z = d2f_bits(rz - int_plus_half(cz) * g.ell[2]);
     cm.w = 0.0f;
     d.com[s] = cm;
     if (m.single_lj_at_com) return;
-    float w = (float)qw, x = (float)qx, y = (float)qy, z = (float)qz;
+    float w = d2f_bits(qw), x = d2f_bits(qx), y = d2f_bits(qy), z = d2f_bits(qz);
     float R[9] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y),
                   2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x),
                   2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)};

@@ -7,13 +7,16 @@
 // written); the rotational increment q_dot (from w = I^-1 A(q) j, the
 // half-step quaternion and its renormalisation) is formed in FP32 from the
 // rounded state, so its relative error (~1e-7) enters q only through the
-// dt-scaled update.  The final renormalisation of q uses the series
+// dt-scaled update.  The FP32 <-> FP64 conversions and the cell floor run
+// as integer bit operations (md_fpconv.cuh, the same bits as the hardware
+// conversions), which keeps them off the FP64 pipe that bounds this step.  The final renormalisation of q uses the series
 // (1 + e)^(-1/2) = 1 - e/2 + 3e^2/8 - 5e^3/16 with e = |q|^2 - 1 where it
 // is exact to FP64 rounding (|e| < 1e-4, the usual case), 1/sqrt(1 + e)
 // otherwise.  No FP64 division is left per molecule: dt/m and 1/ell come
 // from the host.
 #pragma once
 
+#include "md_fpconv.cuh"
 #include "md_internal.cuh"
 
 namespace mdk {
@@ -39,9 +42,10 @@ inline LeapArgs leap_args(const DevModel &m, double dt)
 // x * (1/ell) is within a few ulp of x / ell; cell edges are at least
 // rc (1 + 1e-9), so a molecule that rounding moves across a face lands in a
 // cell from which every partner closer than rc is still in the stencil.
+// The floor is taken on the integer pipe (floor_bits).
 __device__ __forceinline__ int cell_coord(double x, double iell, int nc)
 {
-    const int c = __double2int_rd(x * iell);
+    const int c = floor_bits(x * iell);
     return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
@@ -72,8 +76,8 @@ __device__ __forceinline__ void quat_rate_f(const float q[4], const float w[3], 
 __device__ __forceinline__ float kin_rot2(const double *q, const double (&j)[3], const float (&Iinv)[3],
                                           const float (&Im)[3])
 {
-    const float qf[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
-    const float jf[3] = {(float)j[0], (float)j[1], (float)j[2]};
+    const float qf[4] = {d2f_bits(q[0]), d2f_bits(q[1]), d2f_bits(q[2]), d2f_bits(q[3])};
+    const float jf[3] = {d2f_bits(j[0]), d2f_bits(j[1]), d2f_bits(j[2])};
     float w[3];
     omega_body_f(qf, jf, Iinv, w);
     return Im[0] * w[0] * w[0] + Im[1] * w[1] * w[1] + Im[2] * w[2] * w[2];
@@ -97,7 +101,7 @@ __device__ __forceinline__ bool leapfrog_one(const DevModel &m, const DevState &
     }
     const float fav[3] = {fa.x, fa.y, fa.z}, tav[3] = {ta.x, ta.y, ta.z};
     for (int k = 0; k < 3; k++) {
-        const double F = ACC32 ? (double)fav[k] : d.F[3 * s + k];
+        const double F = ACC32 ? f2d_bits(fav[k]) : d.F[3 * s + k];
         const double v = d.v[3 * s + k] + a.dtm * F;  // Eq. 2
         double r = d.r[3 * s + k] + a.dt * v;         // Eq. 3
         // 0 <= r < L as one unsigned compare of the bit patterns (IEEE order
@@ -116,17 +120,17 @@ __device__ __forceinline__ bool leapfrog_one(const DevModel &m, const DevState &
         double q[4] = {d.q[4 * s], d.q[4 * s + 1], d.q[4 * s + 2], d.q[4 * s + 3]};
         double j[3], t[3];
         float qf[4], tf[3], jh[3], jt[3], w[3], qd[4], qh[4];
-        for (int k = 0; k < 4; k++) qf[k] = (float)q[k];
+        for (int k = 0; k < 4; k++) qf[k] = d2f_bits(q[k]);
         for (int k = 0; k < 3; k++) {
             if (ACC32) {
                 tf[k] = tav[k];
-                t[k] = (double)tf[k];
+                t[k] = f2d_bits(tf[k]);
             } else {
                 t[k] = d.tau[3 * s + k];
                 tf[k] = (float)t[k];
             }
             j[k] = d.j[3 * s + k] + a.dt * t[k];  // Eq. 4: j(t + dt/2), FP64
-            jh[k] = (float)j[k];
+            jh[k] = d2f_bits(j[k]);
             jt[k] = jh[k] - a.hdt * tf[k];  // j(t)
         }
         omega_body_f(qf, jt, a.Iinv, w);
@@ -136,7 +140,7 @@ __device__ __forceinline__ bool leapfrog_one(const DevModel &m, const DevState &
         for (int k = 0; k < 4; k++) qh[k] *= nh;
         omega_body_f(qh, jh, a.Iinv, w);
         quat_rate_f(qh, w, qd);
-        for (int k = 0; k < 4; k++) q[k] += a.dt * (double)qd[k];  // Eq. 5: q(t + dt)
+        for (int k = 0; k < 4; k++) q[k] += a.dt * f2d_bits(qd[k]);  // Eq. 5: q(t + dt)
         const double e = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3] - 1.0;
         // (1 + e)^(-1/2): the cubic series is exact to FP64 rounding for |e| < 1e-4
         const double inv = fabs(e) < 1e-4 ? 1.0 + e * (-0.5 + e * (0.375 - 0.3125 * e)) : 1.0 / sqrt(1.0 + e);
