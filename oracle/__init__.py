@@ -21,6 +21,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "md_oracle.c")
 _HDR = os.path.join(_HERE, "md_oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# a prebuilt library to load instead (the pins' mutation test points this at
+# copies of the oracle with planted mistakes); never rebuilt here
+_LIB_OVERRIDE = os.environ.get("MD_ORACLE_LIB") or None
 _lock = threading.Lock()
 _lib = None
 
@@ -33,6 +36,8 @@ OBS = {"U": 0, "W": 1, "Wxx": 2, "Wyy": 3, "Wzz": 4, "n_mol_pairs": 5, "n_site_p
 
 def build(force: bool = False) -> str:
     """Compile liboracle.so (gcc, -O2, OpenMP) if missing or stale."""
+    if _LIB_OVERRIDE:
+        return _LIB_OVERRIDE
     with _lock:
         stale = (not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
         if force or stale:
@@ -63,8 +68,7 @@ class Setup(C.Structure):
 def _lib_handle():
     global _lib
     if _lib is None:
-        build()
-        lib = C.CDLL(_LIB)
+        lib = C.CDLL(build())
         P = C.POINTER
         d, i64, i32 = C.c_double, C.c_int64, C.c_int
         dp = P(d)
