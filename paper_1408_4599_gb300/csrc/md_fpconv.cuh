@@ -1,9 +1,9 @@
 // md_fpconv.cuh -- FP32 <-> FP64 conversions, k + 1/2 as a double and the
 // floor of a double written as integer bit operations.
 //
-// GB300 executes the hardware conversions (F2F, I2F.F64, F2I.F64) on its
-// FP64 pipe, which runs at a small fraction of the FP32 rate, and the
-// integrator and the rebuild are bound by that pipe.  These forms run on the
+// GB300 executes the hardware conversions (float <-> double, int <->
+// double) on its FP64 pipe, which runs at a small fraction of the FP32
+// rate, and the integrator and the rebuild are bound by that pipe.  These forms run on the
 // integer pipes instead and give the same bits as the hardware's
 // round-to-nearest-even conversions under flush-to-zero, with one stated
 // exception each (d2f_bits: values below FLT_MIN, floor_bits: NaN).  Plain
