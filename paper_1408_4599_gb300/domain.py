@@ -1,23 +1,35 @@
 """Spatial domain decomposition across ranks (§4: subvolumes with halo
 cells, one exchange per step, load balanced by the per-cell cost of Eq. 6).
 
-One process per GPU.  The periodic box is cut into slabs along its longest
-axis; slab boundaries fall on cell planes and are placed so that every rank
-gets an equal share of the load-cost estimate
+One process per GPU.  The periodic box is cut along cell planes into one
+subvolume per rank, balanced by the load-cost estimate
 
-    n_d = sum over cells c of the slab:  N_c / 2 (N_c + sum over the 26 neighbours of c of N_c')
+    n_d = sum over cells c of the subvolume:  N_c / 2 (N_c + sum over the 26 neighbours of c of N_c')
 
 (§4 Eq. 6: the pair work of a cell grows with its own occupation times the
-occupation around it).  Each step a rank
+occupation around it).  Two partitions:
 
-  1. receives from each neighbouring slab the molecules that lie within r_c
-     of its faces (the halo: every partner of an owned molecule inside the
+  * ``kd`` (§4.3, tree-based decomposition): the box is bisected
+    recursively by planes perpendicular to alternating axes, each plane the
+    one of least load imbalance between the two halves (per rank of each
+    half), until every rank has a brick; every brick covers at least
+    ``min_cells`` cells along each axis;
+  * ``slab``: cuts along the longest axis only.
+
+Each step a rank
+
+  1. receives from every other rank the molecules that lie within r_c of
+     its subvolume (the halo: every partner of an owned molecule inside the
      centre-of-mass cut-off is then present locally),
   2. evaluates forces and torques of its owned + halo set on its own GPU with
      the global periodic box (the minimum image is unchanged, so the force on
      an owned molecule is exactly the single-domain force), keeps the owned
      rows, and advances the owned molecules,
-  3. hands molecules that left its slab to the neighbour that now owns them.
+  3. hands molecules that left its subvolume to the rank that now owns them.
+
+``rebalance()`` (dynamic load balancing, §4: every 100 to 1000 steps) sums
+the ranks' cell histograms, recomputes the partition from the current
+occupation and migrates the molecules to their new owners.
 
 Energies, virials and pair counts are pair sums: with A the owned and H the
 halo molecules of a rank, pairs inside A count once and pairs between A and
@@ -51,31 +63,53 @@ def cell_grid(box, rc):
     return [max(1, int(math.floor(L / (rc * (1.0 + 1e-9))))) for L in box]
 
 
-def cell_costs(r, box, rc):
-    """Per-cell load estimate n_d = N_c / 2 (N_c + sum of the 26 neighbours'
-    N) on the linked-cell grid (§4 Eq. 6); returns (costs[nz, ny, nx], nc)."""
+def cell_index(r, box, rc):
+    """Cell coordinates (x, y, z) of each position on the linked-cell grid,
+    periodic wrap included; returns (idx[n, 3], nc)."""
     nc = cell_grid(box, rc)
     L = np.asarray(box, float)
     idx = np.floor(np.mod(r, L) / (L / nc)).astype(np.int64)
-    idx = np.minimum(idx, np.asarray(nc) - 1)
+    return np.clip(idx, 0, np.asarray(nc) - 1), nc
+
+
+def cell_counts(r, box, rc):
+    """Molecules per cell, N[nz, ny, nx]."""
+    idx, nc = cell_index(r, box, rc)
     N = np.zeros((nc[2], nc[1], nc[0]))
     np.add.at(N, (idx[:, 2], idx[:, 1], idx[:, 0]), 1.0)
+    return N
+
+
+def cell_costs(r, box, rc):
+    """Per-cell load estimate n_d = N_c / 2 (N_c + sum of the 26 neighbours'
+    N) on the linked-cell grid (§4 Eq. 6); returns (costs[nz, ny, nx], nc)."""
+    return costs_from_counts(cell_counts(r, box, rc)), cell_grid(box, rc)
+
+
+def costs_from_counts(N):
+    """Eq. 6 from the cell occupation N[nz, ny, nx] (periodic neighbours)."""
     around = np.zeros_like(N)
     for dz in (-1, 0, 1):
         for dy in (-1, 0, 1):
             for dx in (-1, 0, 1):
                 if dx or dy or dz:
                     around += np.roll(N, shift=(dz, dy, dx), axis=(0, 1, 2))
-    return 0.5 * N * (N + around), nc
+    return 0.5 * N * (N + around)
 
 
 def partition(r, box, rc, world):
-    """Slab decomposition along the longest axis: (axis, boundaries) with
-    boundaries[k] .. boundaries[k + 1] the coordinate interval of rank k,
-    cut on cell planes so that the ranks' shares of the Eq. 6 load estimate
-    are as equal as the planes allow, each slab at least one cell (>= r_c)
-    thick."""
-    costs, nc = cell_costs(r, box, rc)
+    """Slab decomposition along the longest axis: (axis, boundaries, shares)
+    with boundaries[k] .. boundaries[k + 1] the coordinate interval of rank
+    k, cut on cell planes so that the ranks' shares of the Eq. 6 load
+    estimate are as equal as the planes allow, each slab at least one cell
+    (>= r_c) thick."""
+    costs, _ = cell_costs(r, box, rc)
+    return partition_slab(costs, box, rc, world)
+
+
+def partition_slab(costs, box, rc, world):
+    """The slab decomposition of `partition` from per-cell costs."""
+    nc = cell_grid(box, rc)
     axis = int(np.argmax(box))
     if world > nc[axis]:
         raise ValueError(f"{world} slabs need at least {world} cells along axis {axis} (have {nc[axis]})")
@@ -93,6 +127,84 @@ def partition(r, box, rc, world):
     return axis, [c * ell for c in cuts], [float(cum[cuts[k + 1]] - cum[cuts[k]]) for k in range(world)]
 
 
+def partition_kd(costs, world, min_cells=2):
+    """Tree-based decomposition (§4.3) of the cell grid with per-cell costs
+    costs[nz, ny, nx] into `world` bricks.  A region holding p ranks is cut
+    by a cell plane perpendicular to the axis of its depth in the tree
+    (x, y, z, x, ...; the next axis when that one admits no plane) into a
+    lower part for p // 2 ranks and an upper part for the rest; of the
+    admissible planes the one with the least load imbalance, the larger of
+    cost / ranks of the two sides, is taken.  A plane is admissible if both
+    parts can in turn be cut the same way into bricks of at least min_cells
+    cells along every axis.  Returns (bricks, shares): bricks[k] =
+    ((x0, y0, z0), (x1, y1, z1)) in cells, half-open, and shares[k] its
+    summed cost.  Raises ValueError if no such decomposition exists."""
+    from functools import lru_cache
+
+    nc = (costs.shape[2], costs.shape[1], costs.shape[0])
+
+    def child_dims(dims, axis, length):
+        d = list(dims)
+        d[axis] = length
+        return tuple(d)
+
+    @lru_cache(maxsize=None)
+    def feasible(dims, p, depth):
+        if p == 1:
+            return all(d >= min_cells for d in dims)
+        p_lo = p // 2
+        for t in range(3):
+            axis = (depth + t) % 3
+            for c in range(1, dims[axis]):
+                if feasible(child_dims(dims, axis, c), p_lo, (depth + 1) % 3) and \
+                        feasible(child_dims(dims, axis, dims[axis] - c), p - p_lo, (depth + 1) % 3):
+                    return True
+        return False
+
+    if world < 1 or not feasible(nc, world, 0):
+        raise ValueError(f"cannot give {world} ranks bricks of at least {min_cells} cells per axis "
+                         f"on a {nc[0]} x {nc[1]} x {nc[2]} cell grid")
+    bricks = [None] * world
+
+    def split(lo, hi, r0, p, depth):
+        if p == 1:
+            bricks[r0] = (tuple(lo), tuple(hi))
+            return
+        p_lo, p_hi = p // 2, p - p // 2
+        dims = tuple(hi[a] - lo[a] for a in range(3))
+        for t in range(3):
+            axis = (depth + t) % 3
+            cuts = [c for c in range(1, dims[axis])
+                    if feasible(child_dims(dims, axis, c), p_lo, (depth + 1) % 3)
+                    and feasible(child_dims(dims, axis, dims[axis] - c), p_hi, (depth + 1) % 3)]
+            if cuts:
+                break
+        sub = costs[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
+        planes = sub.sum(axis=tuple(k for k in range(3) if k != 2 - axis))  # cost per plane along `axis`
+        cum = np.concatenate([[0.0], np.cumsum(planes)])
+        cuts = np.asarray(cuts)
+        worst = np.maximum(cum[cuts] / p_lo, (cum[-1] - cum[cuts]) / p_hi)
+        c = lo[axis] + int(cuts[int(np.argmin(worst))])
+        hi_lo, lo_hi = list(hi), list(lo)
+        hi_lo[axis] = c
+        lo_hi[axis] = c
+        split(lo, hi_lo, r0, p_lo, depth + 1)
+        split(lo_hi, hi, r0 + p_lo, p_hi, depth + 1)
+
+    split([0, 0, 0], list(nc), 0, world, 0)
+    shares = [float(costs[b[0][2]:b[1][2], b[0][1]:b[1][1], b[0][0]:b[1][0]].sum()) for b in bricks]
+    return bricks, shares
+
+
+def _periodic_gap(x, lo, hi, L):
+    """Distance along one periodic axis from coordinates x to the interval
+    [lo, hi) (0 inside it)."""
+    if hi - lo >= L:
+        return np.zeros_like(x)
+    inside = (x >= lo) & (x < hi)
+    return np.where(inside, 0.0, np.minimum(np.mod(lo - x, L), np.mod(x - hi, L)))
+
+
 class Domain:
     """One rank's slab [lo, hi) along `axis` of the periodic box."""
 
@@ -101,6 +213,7 @@ class Domain:
         self.box = np.asarray(box, float)
         self.rc, self.axis = float(rc), axis
         self.lo, self.hi = float(bounds[rank]), float(bounds[rank + 1])
+        self.bounds = list(bounds)
         self.left, self.right = (rank - 1) % world, (rank + 1) % world
 
     def owner(self, r, bounds):
@@ -117,53 +230,98 @@ class Domain:
         d_hi = np.mod(self.hi - x, L)       # distance below the upper face
         return np.nonzero(d_lo < self.rc)[0], np.nonzero(d_hi <= self.rc)[0]
 
+    def halo_routes(self, r):
+        """Indices of the owned molecules each rank needs as its halo."""
+        to_l, to_r = self.halo_out(r)
+        routes = [np.zeros(0, np.int64) for _ in range(self.world)]
+        routes[self.left] = to_l
+        routes[self.right] = np.union1d(routes[self.right], to_r)  # one rank on both sides: once
+        return routes
 
-def _exchange(arrays_to_left, arrays_to_right, domain, dist, group=None):
-    """Sends one dict of arrays to each neighbour and receives theirs
-    (counts first, then float64 payloads; non-blocking pairs, no ordering
-    deadlock).  Host tensors: under NCCL pass a gloo group.  Returns
-    (from_left, from_right)."""
+    def owner_of(self, r):
+        return self.owner(r, self.bounds)
+
+
+class BrickDomain:
+    """One rank's brick of a tree-based decomposition (§4.3): bricks[k] =
+    ((x0, y0, z0), (x1, y1, z1)) in cells of the linked-cell grid."""
+
+    def __init__(self, rank, world, box, rc, bricks):
+        self.rank, self.world = rank, world
+        self.box = np.asarray(box, float)
+        self.rc = float(rc)
+        self.bricks = [tuple(map(tuple, b)) for b in bricks]
+        self.nc = cell_grid(box, rc)
+        self.ell = self.box / np.asarray(self.nc, float)
+        self.grid = np.full((self.nc[2], self.nc[1], self.nc[0]), -1, np.int64)  # owner of each cell
+        for k, (lo, hi) in enumerate(self.bricks):
+            self.grid[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = k
+        if (self.grid < 0).any():
+            raise ValueError("the bricks do not cover the cell grid")
+
+    def owner_of(self, r):
+        """Rank owning each position: the brick of its cell."""
+        idx, _ = cell_index(r, self.box, self.rc)
+        return self.grid[idx[:, 2], idx[:, 1], idx[:, 0]]
+
+    def gap(self, r, k):
+        """Periodic distance of each position from brick k (0 inside)."""
+        lo, hi = self.bricks[k]
+        x = np.mod(r, self.box)
+        g2 = np.zeros(r.shape[0])
+        for a in range(3):
+            g = _periodic_gap(x[:, a], lo[a] * self.ell[a], hi[a] * self.ell[a], self.box[a])
+            g2 += g * g
+        return np.sqrt(g2)
+
+    def halo_routes(self, r):
+        """Indices of the owned molecules within r_c of each other rank's
+        brick: every centre-of-mass partner of a molecule of that brick
+        (minimum image, |X| < r_c) is within r_c of the brick."""
+        routes = [np.zeros(0, np.int64) for _ in range(self.world)]
+        for k in range(self.world):
+            if k != self.rank and r.shape[0]:
+                routes[k] = np.nonzero(self.gap(r, k) <= self.rc * (1.0 + 1e-9))[0]
+        return routes
+
+
+def _exchange(sends, keys, widths, rank, world, dist, group=None):
+    """Sends sends[k] (a dict of arrays with the given keys and row widths,
+    one row per molecule) to rank k and receives what every rank sent here:
+    the counts of all ranks by one all-gather, then the float64 payloads by
+    non-blocking point-to-point pairs (no ordering deadlock).  Host tensors:
+    under NCCL pass a gloo group.  Returns the received rows of all ranks,
+    concatenated in rank order, as one dict."""
     import torch
-    keys = sorted(arrays_to_left)
-    widths = {k: (arrays_to_left[k].shape[1] if arrays_to_left[k].ndim == 2 else 1) for k in keys}
+    width = sum(widths[k] for k in keys)
 
     def pack(d):
-        n = next(iter(d.values())).shape[0]
+        n = d[keys[0]].shape[0]
         return torch.from_numpy(np.concatenate([np.asarray(d[k], float).reshape(n, widths[k]) for k in keys], axis=1)
                                 .reshape(-1).copy()), n
 
-    def unpack(t, n):
-        a = t.numpy().reshape(n, -1) if n else np.zeros((0, sum(widths.values())))
-        out, c = {}, 0
-        for k in keys:
-            w = widths[k]
-            out[k] = a[:, c:c + w] if w > 1 or arrays_to_left[k].ndim == 2 else a[:, c]
-            c += w
-        return out
-
-    pl, nl = pack(arrays_to_left)
-    pr, nr = pack(arrays_to_right)
-    cnt_in_l, cnt_in_r = torch.zeros(1, dtype=torch.int64), torch.zeros(1, dtype=torch.int64)
-    reqs = [dist.isend(torch.tensor([nl], dtype=torch.int64), domain.left, group=group, tag=1),
-            dist.isend(torch.tensor([nr], dtype=torch.int64), domain.right, group=group, tag=2),
-            dist.irecv(cnt_in_r, domain.right, group=group, tag=1), dist.irecv(cnt_in_l, domain.left, group=group, tag=2)]
-    for q in reqs:
-        q.wait()
-    width = sum(widths.values())
-    buf_l = torch.zeros(int(cnt_in_l.item()) * width, dtype=torch.float64)
-    buf_r = torch.zeros(int(cnt_in_r.item()) * width, dtype=torch.float64)
+    packed = [pack(sends[k]) if k != rank else (None, 0) for k in range(world)]
+    mine = torch.tensor([n for _, n in packed], dtype=torch.int64)
+    counts = [torch.zeros(world, dtype=torch.int64) for _ in range(world)]
+    dist.all_gather(counts, mine, group=group)
+    incoming = [int(counts[k][rank].item()) for k in range(world)]  # rows rank k sends here
+    bufs = [torch.zeros(incoming[k] * width, dtype=torch.float64) for k in range(world)]
     reqs = []
-    if nl:
-        reqs.append(dist.isend(pl, domain.left, group=group, tag=3))
-    if nr:
-        reqs.append(dist.isend(pr, domain.right, group=group, tag=4))
-    if buf_r.numel():
-        reqs.append(dist.irecv(buf_r, domain.right, group=group, tag=3))
-    if buf_l.numel():
-        reqs.append(dist.irecv(buf_l, domain.left, group=group, tag=4))
+    for k in range(world):
+        if k != rank and packed[k][1]:
+            reqs.append(dist.isend(packed[k][0], k, group=group, tag=7))
+        if k != rank and incoming[k]:
+            reqs.append(dist.irecv(bufs[k], k, group=group, tag=7))
     for q in reqs:
         q.wait()
-    return unpack(buf_l, int(cnt_in_l.item())), unpack(buf_r, int(cnt_in_r.item()))
+    rows = np.concatenate([b.numpy().reshape(-1, width) for b in bufs], axis=0) if sum(incoming) else \
+        np.zeros((0, width))
+    out, c = {}, 0
+    for k in keys:
+        w = widths[k]
+        out[k] = rows[:, c:c + w] if w > 1 else rows[:, c]
+        c += w
+    return out
 
 
 class DecomposedSystem:
@@ -171,32 +329,49 @@ class DecomposedSystem:
     per-step halo exchange, local evaluation and migration."""
 
     STATE = ("r", "v", "q", "j")
+    KEYS = ("r", "v", "q", "j", "ids")
+    WIDTHS = {"r": 3, "v": 3, "q": 4, "j": 3, "ids": 1}
 
-    def __init__(self, domain, bounds, backend, state, ids, dist, group=None):
+    def __init__(self, domain, bounds, backend, state, ids, dist, group=None, method="slab", min_cells=2):
         self.dom, self.bounds, self.be, self.dist, self.group = domain, bounds, backend, dist, group
         self.st = {k: np.ascontiguousarray(state[k], float) for k in self.STATE}
         self.ids = np.asarray(ids, np.int64)
+        self.method, self.min_cells = method, min_cells
+
+    @staticmethod
+    def make_domain(rank, world, box, rc, counts, method="slab", min_cells=2):
+        """The partition of the cell occupation counts[nz, ny, nx] among
+        `world` ranks by its Eq. 6 costs: (domain, bounds) with bounds the
+        slab boundaries ("slab") or the bricks ("kd")."""
+        costs = costs_from_counts(counts)
+        if method == "kd":
+            bricks, _ = partition_kd(costs, world, min_cells)
+            return BrickDomain(rank, world, box, rc, bricks), bricks
+        if method != "slab":
+            raise ValueError(f"unknown partition {method!r} (slab or kd)")
+        axis, bounds, _ = partition_slab(costs, box, rc, world)
+        return Domain(rank, world, box, rc, axis, bounds), bounds
 
     @classmethod
-    def scatter_from(cls, rank, world, cfg, backend, dist, group=None):
+    def scatter_from(cls, rank, world, cfg, backend, dist, group=None, method="slab", min_cells=2):
         """Every rank holds the same full configuration (seeded input) and
-        keeps the molecules of its slab."""
-        axis, bounds, _ = partition(cfg["r"], cfg["box"], cfg["rc"], world)
-        dom = Domain(rank, world, cfg["box"], cfg["rc"], axis, bounds)
-        mine = np.nonzero(dom.owner(cfg["r"], bounds) == rank)[0]
-        return cls(dom, bounds, backend, {k: cfg[k][mine] for k in cls.STATE}, mine, dist, group)
+        keeps the molecules of its subvolume (method: "slab" or "kd")."""
+        counts = cell_counts(cfg["r"], cfg["box"], cfg["rc"])
+        dom, bounds = cls.make_domain(rank, world, cfg["box"], cfg["rc"], counts, method, min_cells)
+        mine = np.nonzero(dom.owner_of(cfg["r"]) == rank)[0]
+        return cls(dom, bounds, backend, {k: cfg[k][mine] for k in cls.STATE}, mine, dist, group, method, min_cells)
+
+    def _rows(self, ix):
+        return {**{k: self.st[k][ix] for k in self.STATE}, "ids": self.ids[ix].astype(float)}
+
+    def _send(self, routes):
+        return _exchange([self._rows(ix) for ix in routes], self.KEYS, self.WIDTHS, self.dom.rank, self.dom.world,
+                         self.dist, self.group)
 
     def _halo(self):
         if self.dom.world == 1:  # the periodic box itself: no halo
             return {**{k: self.st[k][:0] for k in self.STATE}, "ids": np.zeros(0)}
-        to_l, to_r = self.dom.halo_out(self.st["r"])
-        pick = lambda ix: {**{k: self.st[k][ix] for k in self.STATE}, "ids": self.ids[ix].astype(float)}
-        from_l, from_r = _exchange(pick(to_l), pick(to_r), self.dom, self.dist, self.group)
-        halo = {k: np.concatenate([from_l[k], from_r[k]]) for k in (*self.STATE, "ids")}
-        if self.dom.world == 2:  # both neighbours are the same rank: a molecule near both faces came twice
-            _, keep = np.unique(halo["ids"], return_index=True)
-            halo = {k: v[np.sort(keep)] for k, v in halo.items()}
-        return halo
+        return self._send(self.dom.halo_routes(self.st["r"]))
 
     def forces(self):
         """Forces and torques on the owned molecules (rows in self.ids order)."""
@@ -229,7 +404,7 @@ class DecomposedSystem:
     def step(self, dt, T_target=0.0):
         """One leapfrog step: halo exchange, local step of owned + halo
         (the halo's own update is discarded), migration of the molecules
-        that left the slab.  NVE only when T_target <= 0 (the velocity-
+        that left the subvolume.  NVE only when T_target <= 0 (the velocity-
         rescaling factor needs a global kinetic energy: not offered)."""
         if T_target > 0:
             raise NotImplementedError("velocity rescaling is not offered across domains")
@@ -241,19 +416,29 @@ class DecomposedSystem:
         self._migrate()
 
     def _migrate(self):
+        """Molecules whose owner (by the current partition) is another rank
+        move there, wherever it is."""
         if self.dom.world == 1:
             return
-        own = self.dom.owner(self.st["r"], self.bounds)
-        # after one step a molecule moves far less than a slab: only to a neighbour
-        go_l = np.nonzero(own == self.dom.left)[0]
-        go_r = np.nonzero((own == self.dom.right) & (own != self.dom.left))[0]
+        own = self.dom.owner_of(self.st["r"])
         stay = np.nonzero(own == self.dom.rank)[0]
-        if own.size and np.setdiff1d(np.nonzero(own != self.dom.rank)[0], np.concatenate([go_l, go_r])).size:
-            raise RuntimeError("a molecule moved past a neighbouring slab in one step")
-        pick = lambda ix: {**{k: self.st[k][ix] for k in self.STATE}, "ids": self.ids[ix].astype(float)}
-        from_l, from_r = _exchange(pick(go_l), pick(go_r), self.dom, self.dist, self.group)
-        self.st = {k: np.concatenate([self.st[k][stay], from_l[k], from_r[k]]) for k in self.STATE}
-        self.ids = np.concatenate([self.ids[stay], from_l["ids"].astype(np.int64), from_r["ids"].astype(np.int64)])
+        got = self._send([np.nonzero(own == k)[0] if k != self.dom.rank else np.zeros(0, np.int64)
+                          for k in range(self.dom.world)])
+        self.st = {k: np.concatenate([self.st[k][stay], got[k]]) for k in self.STATE}
+        self.ids = np.concatenate([self.ids[stay], got["ids"].astype(np.int64)])
+
+    def rebalance(self):
+        """Dynamic load balancing (§4: every 100 to 1000 steps): the ranks'
+        cell histograms are summed by one all-reduce, every rank forms the
+        same partition of the current occupation (the method chosen at
+        set-up) and the molecules migrate to their new owners."""
+        import torch
+        box, rc = self.dom.box, self.dom.rc
+        N = torch.from_numpy(cell_counts(self.st["r"], box, rc))
+        self.dist.all_reduce(N, group=self.group)
+        self.dom, self.bounds = self.make_domain(self.dom.rank, self.dom.world, box, rc, N.numpy(), self.method,
+                                                 self.min_cells)
+        self._migrate()
 
 
 class GpuBackend:
