@@ -262,3 +262,28 @@ def test_partition_rejects_more_slabs_than_cell_planes():
     nc = domain.cell_grid(cfg["box"], cfg["rc"])
     with pytest.raises(ValueError):
         domain.partition(cfg["r"], cfg["box"], cfg["rc"], max(nc) + 1)
+
+
+def test_kd_partition_properties_on_random_grids():
+    """On random cell grids and random, partly empty Eq. 6 costs: whenever
+    bricks of at least two cells per axis exist for `world` ranks, they tile
+    the grid, their shares add up to the total, and the brick count fits
+    the grid's volume; otherwise the partition refuses with ValueError."""
+    rng = np.random.default_rng(14080)
+    for _ in range(60):
+        nc = rng.integers(2, 13, size=3)
+        costs = rng.exponential(1.0, size=(nc[2], nc[1], nc[0])) * (rng.random((nc[2], nc[1], nc[0])) < 0.7)
+        world = int(rng.integers(1, 10))
+        try:
+            bricks, shares = domain.partition_kd(costs, world)
+        except ValueError:
+            assert world > 1
+            continue
+        assert len(bricks) == world
+        assert world <= (nc[0] // 2) * (nc[1] // 2) * (nc[2] // 2)
+        cover = np.zeros(costs.shape, dtype=int)
+        for lo, hi in bricks:
+            assert all(hi[a] - lo[a] >= 2 for a in range(3))
+            cover[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] += 1
+        assert (cover == 1).all()
+        assert sum(shares) == pytest.approx(costs.sum())
