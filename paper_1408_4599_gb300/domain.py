@@ -127,7 +127,7 @@ def partition_slab(costs, box, rc, world):
     return axis, [c * ell for c in cuts], [float(cum[cuts[k + 1]] - cum[cuts[k]]) for k in range(world)]
 
 
-def partition_kd(costs, world, min_cells=2):
+def partition_kd(costs, world, min_cells=2, coarse_cells=None):
     """Tree-based decomposition (§4.3) of the cell grid with per-cell costs
     costs[nz, ny, nx] into `world` bricks.  A region holding p ranks is cut
     by a cell plane perpendicular to the axis of its depth in the tree
@@ -136,9 +136,17 @@ def partition_kd(costs, world, min_cells=2):
     admissible planes the one with the least load imbalance, the larger of
     cost / ranks of the two sides, is taken.  A plane is admissible if both
     parts can in turn be cut the same way into bricks of at least min_cells
-    cells along every axis.  Returns (bricks, shares): bricks[k] =
-    ((x0, y0, z0), (x1, y1, z1)) in cells, half-open, and shares[k] its
-    summed cost.  Raises ValueError if no such decomposition exists."""
+    cells along every axis.
+
+    coarse_cells (the simplified first levels of §4.3 for very large
+    volumes): while a region holds more cells than this, it is halved by
+    volume instead (the middle plane of the axis), and its ranks are divided
+    between the halves in proportion to their costs (the nearest division
+    for which both halves can still be decomposed).
+
+    Returns (bricks, shares): bricks[k] = ((x0, y0, z0), (x1, y1, z1)) in
+    cells, half-open, and shares[k] its summed cost.  Raises ValueError if
+    no such decomposition exists."""
     from functools import lru_cache
 
     nc = (costs.shape[2], costs.shape[1], costs.shape[0])
@@ -166,12 +174,43 @@ def partition_kd(costs, world, min_cells=2):
                          f"on a {nc[0]} x {nc[1]} x {nc[2]} cell grid")
     bricks = [None] * world
 
+    def region_cost(lo, hi):
+        return float(costs[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]].sum())
+
+    def coarse_split(lo, hi, p, depth, dims):
+        """Equal-volume halving with ranks in proportion to the halves'
+        costs: (axis, plane, p_lo) or None."""
+        for t in range(3):
+            axis = (depth + t) % 3
+            h = dims[axis] // 2
+            if h < 1:
+                continue
+            d_lo, d_hi = child_dims(dims, axis, h), child_dims(dims, axis, dims[axis] - h)
+            hi_lo = list(hi)
+            hi_lo[axis] = lo[axis] + h
+            total = region_cost(lo, hi)
+            ideal = p * region_cost(lo, hi_lo) / total if total > 0 else p / 2
+            for q in sorted(range(1, p), key=lambda q: (abs(q - ideal), q)):
+                if feasible(d_lo, q, (depth + 1) % 3) and feasible(d_hi, p - q, (depth + 1) % 3):
+                    return axis, lo[axis] + h, q
+        return None
+
     def split(lo, hi, r0, p, depth):
         if p == 1:
             bricks[r0] = (tuple(lo), tuple(hi))
             return
-        p_lo, p_hi = p // 2, p - p // 2
         dims = tuple(hi[a] - lo[a] for a in range(3))
+        if coarse_cells is not None and dims[0] * dims[1] * dims[2] > coarse_cells:
+            cs = coarse_split(lo, hi, p, depth, dims)
+            if cs is not None:
+                axis, c, q = cs
+                hi_lo, lo_hi = list(hi), list(lo)
+                hi_lo[axis] = c
+                lo_hi[axis] = c
+                split(lo, hi_lo, r0, q, depth + 1)
+                split(lo_hi, hi, r0 + q, p - q, depth + 1)
+                return
+        p_lo, p_hi = p // 2, p - p // 2
         for t in range(3):
             axis = (depth + t) % 3
             cuts = [c for c in range(1, dims[axis])

@@ -287,3 +287,26 @@ def test_kd_partition_properties_on_random_grids():
             cover[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] += 1
         assert (cover == 1).all()
         assert sum(shares) == pytest.approx(costs.sum())
+
+
+def test_kd_coarse_levels_halve_by_volume_and_share_ranks_by_cost():
+    """The simplified first levels of §4.3 for very large volumes: a region
+    larger than `coarse_cells` is halved at its middle plane, and its ranks
+    go to the halves in proportion to their costs; smaller regions are cut
+    by the least-imbalance plane as before."""
+    nc = (16, 8, 8)
+    costs = np.ones((nc[2], nc[1], nc[0]))
+    costs[:, :, :4] += 5.0  # the lower x half carries 3/4 of the load
+    bricks, shares = domain.partition_kd(costs, 8, coarse_cells=16 * 8 * 8 - 1)
+    lower = [b for b in bricks if b[1][0] <= 8]
+    assert all(b[0][0] >= 8 or b[1][0] <= 8 for b in bricks)  # nothing straddles the middle plane
+    assert len(lower) == 6  # 8 ranks x 3/4 of the cost
+    cover = np.zeros(costs.shape, dtype=int)
+    for lo, hi in bricks:
+        cover[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] += 1
+    assert (cover == 1).all()
+    # without coarse levels the first cut is the least-imbalance plane for
+    # 4 + 4 ranks instead: x = 3, where the cost is halved
+    exact, _ = domain.partition_kd(costs, 8)
+    assert sum(1 for b in exact if b[1][0] <= 3) == 4
+    assert all(b[0][0] >= 3 or b[1][0] <= 3 for b in exact)
