@@ -371,11 +371,15 @@ class DecomposedSystem:
     KEYS = ("r", "v", "q", "j", "ids")
     WIDTHS = {"r": 3, "v": 3, "q": 4, "j": 3, "ids": 1}
 
-    def __init__(self, domain, bounds, backend, state, ids, dist, group=None, method="slab", min_cells=2):
+    def __init__(self, domain, bounds, backend, state, ids, dist, group=None, method="slab", min_cells=2,
+                 rebalance_every=0):
+        """rebalance_every: repartition every that many steps (§4: every 100
+        to 1000 steps; 0 = only when rebalance() is called)."""
         self.dom, self.bounds, self.be, self.dist, self.group = domain, bounds, backend, dist, group
         self.st = {k: np.ascontiguousarray(state[k], float) for k in self.STATE}
         self.ids = np.asarray(ids, np.int64)
         self.method, self.min_cells = method, min_cells
+        self.rebalance_every, self.n_steps = int(rebalance_every), 0
 
     @staticmethod
     def make_domain(rank, world, box, rc, counts, method="slab", min_cells=2):
@@ -392,13 +396,15 @@ class DecomposedSystem:
         return Domain(rank, world, box, rc, axis, bounds), bounds
 
     @classmethod
-    def scatter_from(cls, rank, world, cfg, backend, dist, group=None, method="slab", min_cells=2):
+    def scatter_from(cls, rank, world, cfg, backend, dist, group=None, method="slab", min_cells=2,
+                     rebalance_every=0):
         """Every rank holds the same full configuration (seeded input) and
         keeps the molecules of its subvolume (method: "slab" or "kd")."""
         counts = cell_counts(cfg["r"], cfg["box"], cfg["rc"])
         dom, bounds = cls.make_domain(rank, world, cfg["box"], cfg["rc"], counts, method, min_cells)
         mine = np.nonzero(dom.owner_of(cfg["r"]) == rank)[0]
-        return cls(dom, bounds, backend, {k: cfg[k][mine] for k in cls.STATE}, mine, dist, group, method, min_cells)
+        return cls(dom, bounds, backend, {k: cfg[k][mine] for k in cls.STATE}, mine, dist, group, method, min_cells,
+                   rebalance_every)
 
     def _rows(self, ix):
         return {**{k: self.st[k][ix] for k in self.STATE}, "ids": self.ids[ix].astype(float)}
@@ -447,6 +453,9 @@ class DecomposedSystem:
         rescaling factor needs a global kinetic energy: not offered)."""
         if T_target > 0:
             raise NotImplementedError("velocity rescaling is not offered across domains")
+        if self.rebalance_every > 0 and self.n_steps > 0 and self.n_steps % self.rebalance_every == 0:
+            self.rebalance()
+        self.n_steps += 1
         halo = self._halo()
         n = self.ids.shape[0]
         full = {k: np.concatenate([self.st[k], halo[k]]) for k in self.STATE}

@@ -70,12 +70,13 @@ CASES = {
 }
 
 
-def _rank_main(rank, world, port, case, n_steps, out, method="slab", rebalance_at=-1):
+def _rank_main(rank, world, port, case, n_steps, out, method="slab", rebalance_at=-1, rebalance_every=0):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     cfg = CASES[case]()
-    ds = domain.DecomposedSystem.scatter_from(rank, world, cfg, OracleBackend(cfg), dist, method=method)
+    ds = domain.DecomposedSystem.scatter_from(rank, world, cfg, OracleBackend(cfg), dist, method=method,
+                                              rebalance_every=rebalance_every)
     F, tau = ds.forces()
     obs = ds.observables()
     res = {"ids0": ds.ids.copy(), "F": F, "tau": tau, "obs": obs, "bounds": ds.bounds}
@@ -92,11 +93,11 @@ def _rank_main(rank, world, port, case, n_steps, out, method="slab", rebalance_a
     dist.destroy_process_group()
 
 
-def _run(case, world, n_steps=0, method="slab", rebalance_at=-1):
+def _run(case, world, n_steps=0, method="slab", rebalance_at=-1, rebalance_every=0):
     with mp.Manager() as mgr:
         out = mgr.dict()
-        mp.spawn(_rank_main, args=(world, _free_port(), case, n_steps, out, method, rebalance_at), nprocs=world,
-                 join=True)
+        mp.spawn(_rank_main, args=(world, _free_port(), case, n_steps, out, method, rebalance_at, rebalance_every),
+                 nprocs=world, join=True)
         return [out[k] for k in range(world)]
 
 
@@ -130,6 +131,25 @@ def test_decomposed_forces_and_observables_equal_single_domain(case, world, meth
     assert obs["n_mol_pairs"] == pytest.approx(o["n_mol_pairs"], abs=1e-9)
     for k in ("U", "W", "Wxx", "Wyy", "Wzz"):
         assert obs[k] == pytest.approx(o[k], rel=1e-11, abs=1e-9 * o["abs_W"]), k
+
+
+def test_slab_trajectory_with_periodic_rebalancing():
+    """Six NVE steps of the boosted slab on three slabs repartitioned every
+    two steps (rebalance_every): the state gathered by global id equals the
+    single-domain trajectory and every molecule ends on the rank whose slab
+    holds it."""
+    n_steps = 6
+    res = _run("slab-fast", 3, n_steps, method="slab", rebalance_every=2)
+    cfg, _, _, _, st = _single("slab-fast", n_steps)
+    ids = np.concatenate([r["ids"] for r in res])
+    assert np.array_equal(np.sort(ids), np.arange(cfg["r"].shape[0]))
+    assert all(r["owned_here"] for r in res)
+    L = np.asarray(cfg["box"])
+    for k in ("r", "v", "q", "j"):
+        d = np.concatenate([r[k] for r in res]) - st[k][ids]
+        if k == "r":
+            d -= L * np.rint(d / L)
+        assert np.abs(d).max() <= 1e-9 * max(1.0, np.abs(st[k]).max()), k
 
 
 def test_decomposed_trajectory_with_migration():
